@@ -1,0 +1,426 @@
+"""Pins for the CPU oracle: closed forms, identities and invariants that fix what it computes
+independently of its own code. Runs without a GPU."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erf, gamma, gammainc
+
+from oracle import dfrhf
+from paper_1707_03771_gb300 import clusters
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(1234)
+
+
+# --------------------------------------------------------------------------- Boys function
+
+@pytest.mark.parametrize("T", [0.0, 1e-12, 1e-6, 0.3, 1.7, 9.5, 25.0, 39.99, 40.01, 55.0, 130.0, 900.0])
+def test_boys_incomplete_gamma(T):
+    """F_m(T) = Gamma(m+1/2) P(m+1/2, T) / (2 T^(m+1/2)), with P the regularised lower incomplete gamma."""
+    F = dfrhf.boys(8, T)
+    for m in range(9):
+        if T == 0.0:
+            ref = 1.0 / (2 * m + 1)
+        elif T < 1e-5:   # Taylor series of exp(-T t^2) integrated term by term
+            ref = sum((-T) ** k / (math.factorial(k) * (2 * m + 2 * k + 1)) for k in range(6))
+        else:
+            ref = gamma(m + 0.5) * gammainc(m + 0.5, T) / (2 * T ** (m + 0.5))
+        assert abs(F[m] - ref) <= 2e-14 * max(ref, 1e-300) + 1e-300, (m, T, F[m], ref)
+
+
+def test_boys_f0_erf_and_asymptote():
+    for T in [0.05, 0.5, 3.0, 12.0, 33.0, 60.0]:
+        assert abs(dfrhf.boys(0, T)[0] - 0.5 * math.sqrt(math.pi / T) * erf(math.sqrt(T))) < 1e-15
+    T = 300.0
+    F = dfrhf.boys(7, T)
+    for m in range(8):
+        dfact = np.prod(np.arange(2 * m - 1, 0, -2)) if m > 0 else 1.0
+        asym = dfact / 2 ** (m + 1) * math.sqrt(math.pi / T ** (2 * m + 1))
+        assert abs(F[m] / asym - 1) < 1e-13
+
+
+def test_boys_downward_identity():
+    for T in [0.2, 5.0, 38.0, 45.0, 80.0]:
+        F = dfrhf.boys(9, T)
+        for m in range(9):
+            assert abs(F[m] - (2 * T * F[m + 1] + math.exp(-T)) / (2 * m + 1)) <= 1e-14 * F[m]
+
+
+# --------------------------------------------------------------------------- s-type closed forms
+
+def _rand_centre(scale=1.5):
+    return rng.uniform(-scale, scale, 3)
+
+
+S0 = (0, 0, 0)
+
+
+def test_s_closed_forms():
+    for _ in range(20):
+        a, b, c, d = np.exp(rng.uniform(np.log(0.05), np.log(50.0), 4))
+        A, B, C, D, Cn = (_rand_centre() for _ in range(5))
+        p, q = a + b, c + d
+        mu = a * b / p
+        RAB2 = np.sum((A - B) ** 2)
+        Kab = math.exp(-mu * RAB2)
+        P = (a * A + b * B) / p
+        Q = (c * C + d * D) / q
+        # overlap and kinetic (Helgaker eq. 9.2.41-9.3.x closed forms for s functions)
+        S = (math.pi / p) ** 1.5 * Kab
+        assert abs(dfrhf.prim_overlap(S0, a, A, S0, b, B) - S) <= 1e-14 * S + 1e-300
+        T = mu * (3 - 2 * mu * RAB2) * S
+        assert abs(dfrhf.prim_kinetic(S0, a, A, S0, b, B) - T) <= 1e-13 * mu * (3 + 2 * mu * RAB2) * S + 1e-300
+        # nuclear attraction: 2 pi / p K_ab F0(p |P - C|^2)
+        V = 2 * math.pi / p * Kab * dfrhf.boys(0, p * np.sum((P - Cn) ** 2))[0]
+        assert abs(dfrhf.prim_potential(S0, a, A, S0, b, B, Cn) - V) <= 1e-13 * V
+        # two-centre: 2 pi^{5/2} / (a b sqrt(a+b)) F0(ab/(a+b) R^2)
+        two = 2 * math.pi ** 2.5 / (a * b * math.sqrt(a + b)) * dfrhf.boys(0, a * b / (a + b) * RAB2)[0]
+        assert abs(dfrhf.prim_eri(S0, a, A, S0, 0.0, A, S0, b, B, S0, 0.0, B) - two) <= 1e-13 * two
+        # three-centre (s|ss) and four-centre (ss|ss)
+        Kcd = math.exp(-c * d / q * np.sum((C - D) ** 2))
+        three = 2 * math.pi ** 2.5 / (c * p * math.sqrt(c + p)) * Kab * dfrhf.boys(0, c * p / (c + p) * np.sum((C - P) ** 2))[0]
+        assert abs(dfrhf.prim_3c(S0, c, C, S0, a, A, S0, b, B) - three) <= 1e-13 * three
+        four = 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * Kab * Kcd * dfrhf.boys(0, p * q / (p + q) * np.sum((P - Q) ** 2))[0]
+        assert abs(dfrhf.prim_eri(S0, a, A, S0, b, B, S0, c, C, S0, d, D) - four) <= 1e-13 * four + 1e-300
+
+
+# --------------------------------------------------------------------------- higher l from centre derivatives
+
+def _richardson(f, x0, h):
+    def cd(hh):
+        return (f(x0 + hh) - f(x0 - hh)) / (2 * hh)
+    return (4 * cd(h / 2) - cd(h)) / 3
+
+
+def _raise_power(fn, centres, exps, powers, which, axis):
+    """x_A^{i+1} g = (1/2a) (d/dA_x [x_A^i g] + i x_A^{i-1} g), with A = centres[which]."""
+    a = exps[which]
+    i = powers[which][axis]
+
+    def f_at(shift):
+        cs = [np.array(c, dtype=float) for c in centres]
+        cs[which][axis] += shift
+        return fn(cs, powers)
+    deriv = _richardson(f_at, 0.0, 2e-3)
+    low = 0.0
+    if i > 0:
+        pl = [list(p) for p in powers]
+        pl[which][axis] -= 1
+        low = i * fn([np.array(c, dtype=float) for c in centres], pl)
+    return (deriv + low) / (2 * a)
+
+
+@pytest.mark.parametrize("kind", ["overlap", "potential", "three", "four"])
+def test_centre_derivative_raises_l(kind):
+    """A Cartesian power raised by one equals a centre derivative of the lower function (exact
+    identity of Gaussians); checked with Richardson-extrapolated finite differences."""
+    for trial in range(6):
+        if kind == "overlap":
+            nc = 2
+            Cn = None
+        elif kind == "potential":
+            nc = 2
+            Cn = _rand_centre()
+        elif kind == "three":
+            nc = 3
+        else:
+            nc = 4
+        exps = list(np.exp(rng.uniform(np.log(0.2), np.log(3.0), nc)))
+        centres = [_rand_centre(1.0) for _ in range(nc)]
+        powers = [list(rng.integers(0, 2, 3)) for _ in range(nc)]
+
+        def fn(cs, pw):
+            if kind == "overlap":
+                return dfrhf.prim_overlap(pw[0], exps[0], cs[0], pw[1], exps[1], cs[1])
+            if kind == "potential":
+                return dfrhf.prim_potential(pw[0], exps[0], cs[0], pw[1], exps[1], cs[1], Cn)
+            if kind == "three":
+                return dfrhf.prim_3c(pw[0], exps[0], cs[0], pw[1], exps[1], cs[1], pw[2], exps[2], cs[2])
+            return dfrhf.prim_eri(pw[0], exps[0], cs[0], pw[1], exps[1], cs[1], pw[2], exps[2], cs[2],
+                                  pw[3], exps[3], cs[3])
+        which = int(rng.integers(0, nc))
+        axis = int(rng.integers(0, 3))
+        up = [list(p) for p in powers]
+        up[which][axis] += 1
+        direct = fn(centres, up)
+        via = _raise_power(fn, centres, exps, powers, which, axis)
+        scale = max(abs(direct), abs(fn(centres, powers)), 1e-3)
+        assert abs(direct - via) <= 2e-8 * scale, (kind, trial, direct, via)
+
+
+def test_point_charge_limit():
+    """A tight s function of exponent alpha tends to (pi/alpha)^{3/2} times a point charge; the
+    three-centre integral then tends to the nuclear-attraction integral (error O(1/alpha))."""
+    for _ in range(4):
+        a, b = np.exp(rng.uniform(np.log(0.3), np.log(2.0), 2))
+        A, B, C = _rand_centre(), _rand_centre(), _rand_centre()
+        pa, pb = list(rng.integers(0, 3, 3)), list(rng.integers(0, 2, 3))
+        V = dfrhf.prim_potential(pa, a, A, pb, b, B, C)
+
+        def f(alpha):
+            return dfrhf.prim_3c(S0, alpha, C, pa, a, A, pb, b, B) / (math.pi / alpha) ** 1.5
+        extrap = 2 * f(2e5) - f(1e5)
+        assert abs(extrap - V) <= 1e-7 * max(abs(V), 1e-3)
+
+
+# --------------------------------------------------------------------------- solid harmonics
+
+def _read_golden_harmonics():
+    rows = {}
+    with open(os.path.join(GOLDEN, "solid_harmonics_l3.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            parts = line.split()
+            l, m = int(parts[0]), int(parts[1])
+            poly = {}
+            for t in parts[2:]:
+                c, pw = t.split(":")
+                poly[tuple(int(x) for x in pw.split(","))] = float(c)
+            rows[(l, m)] = poly
+    return rows
+
+
+def test_solid_harmonics_match_textbook_table():
+    gold = _read_golden_harmonics()
+    for l in range(4):
+        cs, pw = dfrhf.solid_harmonic_coeffs(l)
+        for m in range(-l, l + 1):
+            got = {tuple(pw[k]): cs[m + l, k] for k in range(len(pw)) if abs(cs[m + l, k]) > 1e-14}
+            ref = gold[(l, m)]
+            assert set(got) == set(ref), (l, m)
+            for key in ref:
+                assert abs(got[key] - ref[key]) < 1e-12, (l, m, key)
+
+
+def _poly_eval(cs, pw, pts):
+    mon = np.stack([np.prod(pts ** p, axis=1) for p in pw], axis=1)
+    return mon @ cs.T
+
+
+def test_solid_harmonics_harmonic_and_equal_norm():
+    for l in range(4):
+        cs, pw = dfrhf.solid_harmonic_coeffs(l)
+        # Laplacian of each polynomial vanishes
+        for m in range(2 * l + 1):
+            lap = {}
+            for k, p in enumerate(pw):
+                for ax in range(3):
+                    if p[ax] >= 2:
+                        q = list(p)
+                        q[ax] -= 2
+                        lap[tuple(q)] = lap.get(tuple(q), 0.0) + cs[m, k] * p[ax] * (p[ax] - 1)
+            assert all(abs(v) < 1e-12 for v in lap.values()), (l, m)
+        # every m component has the same normalisation constant
+        for a in [0.1, 1.3, 40.0]:
+            n = dfrhf.sph_norms(l, a)
+            assert np.allclose(n, n[0], rtol=1e-13, atol=0)
+
+
+def _wigner_from_harmonics(l, R):
+    """Matrix D with S_m(R x) = sum_m' D_mm' S_m'(x), fitted on random points."""
+    cs, pw = dfrhf.solid_harmonic_coeffs(l)
+    pts = rng.normal(size=(64, 3))
+    A = _poly_eval(cs, pw, pts)
+    Bm = _poly_eval(cs, pw, pts @ R.T)
+    D, res, *_ = np.linalg.lstsq(A, Bm, rcond=None)
+    assert np.allclose(A @ D, Bm, atol=1e-10)   # the span is rotation invariant
+    return D.T
+
+
+def _random_rotation():
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+def _shell_system(specs):
+    """System with explicit shells [(l, exponent, centre)], one dummy atom."""
+    atoms = np.zeros(1, dtype=clusters.ATOM_DTYPE)
+    atoms["Z"] = 2
+    return np.array([(0, l, a, tuple(c)) for l, a, c in specs], dtype=clusters.SHELL_DTYPE), atoms
+
+
+def test_three_center_rotation_translation_and_index_symmetry():
+    R = _random_rotation()
+    shift = np.array([0.7, -1.1, 0.4])
+    for lp, lm, ln in [(3, 2, 2), (2, 2, 1), (1, 0, 2), (3, 1, 0)]:
+        cP, cM, cN = _rand_centre(), _rand_centre(), _rand_centre()
+        aP, aM, aN = 0.9, 0.6, 1.7
+        basis, atoms = _shell_system([(lm, aM, cM), (ln, aN, cN)])
+        aux, _ = _shell_system([(lp, aP, cP)])
+        sysA = clusters.System(atoms=atoms, basis=basis, aux=aux)
+        blk = dfrhf.three_center_triples(sysA, [(0, 0, 1), (0, 1, 0)])
+        assert np.allclose(blk[0], blk[1].transpose(0, 2, 1), atol=1e-15, rtol=0)
+        basis_r, _ = _shell_system([(lm, aM, R @ cM), (ln, aN, R @ cN)])
+        aux_r, _ = _shell_system([(lp, aP, R @ cP)])
+        rot = dfrhf.three_center_triples(clusters.System(atoms=atoms, basis=basis_r, aux=aux_r), [(0, 0, 1)])[0]
+        DP, DM, DN = (_wigner_from_harmonics(l, R) for l in (lp, lm, ln))
+        # normalised functions: the fitted D maps unnormalised harmonics; norms are m-independent
+        pred = np.einsum("ap,bm,cn,pmn->abc", DP, DM, DN, blk[0])
+        assert np.abs(pred - rot).max() < 1e-12 * max(1.0, np.abs(blk[0]).max())
+        basis_t, _ = _shell_system([(lm, aM, cM + shift), (ln, aN, cN + shift)])
+        aux_t, _ = _shell_system([(lp, aP, cP + shift)])
+        tr = dfrhf.three_center_triples(clusters.System(atoms=atoms, basis=basis_t, aux=aux_t), [(0, 0, 1)])[0]
+        assert np.abs(tr - blk[0]).max() < 1e-13
+
+
+def test_overlap_diagonal_blocks_identity():
+    sysw = clusters.water_cluster(1, 3)
+    S = dfrhf.overlap(sysw)
+    off = 0
+    for sh in sysw.basis:
+        k = 2 * sh["l"] + 1
+        assert np.allclose(S[off:off + k, off:off + k], np.eye(k), atol=1e-13)
+        off += k
+    V = dfrhf.metric(sysw)
+    assert np.allclose(V, V.T, atol=1e-13)
+    assert np.linalg.eigvalsh(V).min() > 0
+
+
+# --------------------------------------------------------------------------- density-fitting layer
+
+def test_df_exact_for_product_complete_aux():
+    """H2 with one s per atom; the auxiliary set spans every orbital product, so DF J and K equal the
+    conventional four-index J and K up to the conditioning of the metric."""
+    sysh = clusters.h2_system(1.4, alpha=0.8)
+    B = dfrhf.whiten(dfrhf.three_center(sysh), dfrhf.metric(sysh))
+    eri = dfrhf.four_center(sysh)
+    C = np.linalg.qr(rng.normal(size=(2, 1)))[0]
+    D = 2 * C @ C.T
+    assert np.abs(dfrhf.df_J(B, D) - dfrhf.conv_J(eri, D)).max() < 1e-10
+    assert np.abs(dfrhf.df_K(B, C) - dfrhf.conv_K(eri, C)).max() < 1e-10
+
+
+def test_df_coulomb_variational_and_monotone():
+    """Coulomb-metric fitting underestimates the Coulomb energy, and a larger auxiliary set (a
+    superset) raises the fitted energy towards the exact value."""
+    sysw = clusters.water_cluster(1, 7)
+    # a smaller orbital basis keeps the four-index reference quick
+    sysw.basis = sysw.basis[sysw.basis["l"] <= 1]
+    n = dfrhf.nfunc(sysw.basis)
+    C = np.linalg.qr(rng.normal(size=(n, 5)))[0]
+    D = 2 * C @ C.T
+    eri = dfrhf.four_center(sysw)
+    e_exact = 0.5 * np.sum(D * dfrhf.conv_J(eri, D))
+    energies = []
+    for lmax in (0, 1, 2, 3):
+        aux = sysw.aux[sysw.aux["l"] <= lmax]
+        s2 = clusters.System(atoms=sysw.atoms, basis=sysw.basis, aux=aux)
+        B = dfrhf.whiten(dfrhf.three_center(s2), dfrhf.metric(s2))
+        energies.append(0.5 * np.sum(D * dfrhf.df_J(B, D)))
+    assert all(e <= e_exact + 1e-10 for e in energies)
+    assert all(energies[i] <= energies[i + 1] + 1e-10 for i in range(3))
+    assert energies[-1] > energies[0]
+
+
+# --------------------------------------------------------------------------- SCF
+
+def test_h2_closed_form_energy():
+    """One s Gaussian per H: the occupied orbital is fixed by symmetry, so the RHF energy follows
+    from the s-type closed forms; the product-complete auxiliary set makes DF exact."""
+    R, a = 1.4, 0.8
+    sysh = clusters.h2_system(R, alpha=a)
+    res = dfrhf.scf(sysh)
+    N = (2 * a / math.pi) ** 0.75
+    s12 = N * N * (math.pi / (2 * a)) ** 1.5 * math.exp(-a / 2 * R * R)
+    t11 = N * N * (a / 2) * 3 * (math.pi / (2 * a)) ** 1.5
+    t12 = N * N * (a / 2) * (3 - a * R * R) * (math.pi / (2 * a)) ** 1.5 * math.exp(-a / 2 * R * R)
+    F0 = lambda T: 1.0 if T == 0 else 0.5 * math.sqrt(math.pi / T) * erf(math.sqrt(T))
+    pref = 2 * math.pi / (2 * a)
+    v11 = -N * N * pref * (F0(0) + F0(2 * a * R * R))
+    v12 = -N * N * pref * math.exp(-a / 2 * R * R) * 2 * F0(2 * a * (R / 2) ** 2)
+    h11, h12 = t11 + v11, t12 + v12
+
+    def eri(A, B, C, D):
+        cen = np.array([0.0, R])
+        P = (cen[A] + cen[B]) / 2
+        Q = (cen[C] + cen[D]) / 2
+        K = math.exp(-a / 2 * (cen[A] - cen[B]) ** 2) * math.exp(-a / 2 * (cen[C] - cen[D]) ** 2)
+        p = q = 2 * a
+        return N ** 4 * 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * K * F0(p * q / (p + q) * (P - Q) ** 2)
+    c = 1 / math.sqrt(2 * (1 + s12))
+    hs = c * c * (2 * h11 + 2 * h12)
+    Js = 0.0
+    for A in range(2):
+        for B in range(2):
+            for C in range(2):
+                for D in range(2):
+                    Js += c ** 4 * eri(A, B, C, D)
+    e = 2 * hs + Js + 1.0 / R
+    assert abs(res.energy - e) < 1e-10, (res.energy, e)
+
+
+def _water_rotated(sysw, R, shift):
+    atoms = sysw.atoms.copy()
+    atoms["xyz"] = atoms["xyz"] @ R.T + shift
+    return clusters.make_system(atoms)
+
+
+@pytest.fixture(scope="module")
+def water1_result():
+    sysw = clusters.water_cluster(1, 11)
+    return sysw, dfrhf.scf(sysw)
+
+
+def test_scf_density_invariants(water1_result):
+    sysw, res = water1_result
+    assert res.converged
+    S = dfrhf.overlap(sysw)
+    D = res.D
+    assert abs(np.trace(D @ S) - sysw.n_electrons) < 1e-10
+    assert np.abs(D @ S @ D - 2 * D).max() < 1e-10
+    assert np.abs(res.J - res.J.T).max() < 1e-12 and np.abs(res.K - res.K.T).max() < 1e-12
+    comm = res.F @ D @ S - S @ D @ res.F
+    assert np.abs(comm).max() < 1e-6
+    # exchange of the occupied orbitals is invariant under a rotation among them
+    B = dfrhf.whiten(dfrhf.three_center(sysw), dfrhf.metric(sysw))
+    Cocc = res.C[:, :sysw.nocc]
+    Q = np.linalg.qr(rng.normal(size=(sysw.nocc, sysw.nocc)))[0]
+    assert np.abs(dfrhf.df_K(B, Cocc) - dfrhf.df_K(B, Cocc @ Q)).max() < 1e-12
+
+
+def test_scf_energy_rigid_motion_invariance(water1_result):
+    sysw, res = water1_result
+    R = _random_rotation()
+    moved = _water_rotated(sysw, R, np.array([1.3, -0.2, 2.9]))
+    assert abs(dfrhf.scf(moved).energy - res.energy) < 1e-10
+
+
+def test_scf_energy_permutation_invariance():
+    sysw = clusters.water_cluster(2, 21)
+    e1 = dfrhf.scf(sysw).energy
+    atoms = np.concatenate([sysw.atoms[3:], sysw.atoms[:3]])
+    e2 = dfrhf.scf(clusters.make_system(atoms)).energy
+    assert abs(e1 - e2) < 1e-10
+
+
+def test_nuclear_repulsion_closed_form():
+    atoms = np.zeros(3, dtype=clusters.ATOM_DTYPE)
+    atoms["xyz"] = [[0, 0, 0], [3, 0, 0], [0, 4, 0]]
+    atoms["Z"] = [8, 1, 2]
+    assert abs(dfrhf.nuclear_repulsion(atoms) - (8 / 3 + 16 / 4 + 2 / 5)) < 1e-14
+
+
+def test_generator_counts_and_geometry():
+    s = clusters.workload("water2")
+    assert (s.nbf, s.naux, s.nocc) == (100, 274, 10)
+    big = clusters.water_cluster(32, 1)
+    assert (big.nbf, big.naux, big.nocc) == (1600, 4384, 160)
+    xyz = big.atoms["xyz"] / clusters.BOHR_PER_ANGSTROM
+    O = xyz[0::3]
+    d = np.linalg.norm(O[:, None] - O[None], axis=-1) + np.eye(32) * 10
+    assert d.min() >= 2.6 - 1e-12
+    for w in range(32):
+        r1 = np.linalg.norm(xyz[3 * w + 1] - xyz[3 * w])
+        r2 = np.linalg.norm(xyz[3 * w + 2] - xyz[3 * w])
+        v1, v2 = xyz[3 * w + 1] - xyz[3 * w], xyz[3 * w + 2] - xyz[3 * w]
+        ang = math.degrees(math.acos(np.dot(v1, v2) / (r1 * r2)))
+        assert abs(r1 - 0.96) < 1e-12 and abs(r2 - 0.96) < 1e-12 and abs(ang - 104.5) < 1e-9
+    # SplitMix64 reference values: seed 0 first output (published test vector)
+    assert clusters.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
