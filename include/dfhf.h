@@ -1,0 +1,153 @@
+/*
+ * dfhf.h -- C ABI of the GB300 density-fitted restricted Hartree-Fock library (libdfhf.so).
+ *
+ * What the library computes (paper, arXiv:1707.03771):
+ *   - every mean-field algorithm rests on density fitting (section "Program features");
+ *   - the three-index tensor I_{gamma,rs} is held in memory (section "Density fitting utilities");
+ *   - its operations, eqs. (1)-(3): index transformation (eq. 1), contraction of two fitted objects
+ *     into a matrix (eq. 2, first form) and contraction with a density matrix (eq. 3, first two forms);
+ *   - integrals are built from shell objects, the nuclear attraction also from the molecule
+ *     (section "Molecular integrals").
+ * Here: I = B_{P,mu nu} = sum_Q (L^-1)_{PQ} (Q|mu nu) with (P|Q) = L L^T (eq. 1, third form, M' = L^-1),
+ *   gamma_P = sum B_{P,mu nu} D_{mu nu}, J = sum_P gamma_P B_P           (eq. 3, first and second forms)
+ *   Y_{P,mu i} = sum_nu B_{P,mu nu} C_{nu i}, K = sum_{P,i} Y Y^T        (eq. 1 first form, eq. 2 first form)
+ *   F = H + J - K, E = 1/2 tr(D(H + F)) + E_nuc, D = 2 C_occ C_occ^T    (RHF, section "Standard algorithms").
+ * K as defined here is the exchange of the occupied orbitals (half the exchange matrix of D).
+ *
+ * Conventions (all functions):
+ *   - Units: bohr and hartree. Shells are uncontracted real-solid-harmonic Gaussians, normalised to
+ *     unit self-overlap; functions are ordered by shell, and within a shell m = -l..l.
+ *   - Matrices are dense row-major doubles; symmetric inputs must be symmetric.
+ *   - Host pointers are owned by the caller and only read/written during the call.
+ *   - Device memory is owned by the handle and released by df_free.
+ *   - Return value: DF_OK (0) or a negative DF_E* code; df_strerror gives its text, and
+ *     df_last_error gives the detail of the last failure on that handle. No C++ exception crosses
+ *     this interface.
+ *   - One GPU: every call runs on the device that was current at df_init, on the handle's stream.
+ */
+#ifndef DFHF_H
+#define DFHF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DF_OK 0
+#define DF_E_ARG (-1)        /* invalid argument (bad shell, l out of range, null pointer, size) */
+#define DF_E_NOMEM (-2)      /* device allocation failed (e.g. B does not fit in HBM) */
+#define DF_E_CUDA (-3)       /* CUDA runtime or cuSOLVER error */
+#define DF_E_NOTCONV (-4)    /* SCF did not converge in max_iter iterations */
+#define DF_E_STATE (-5)      /* call out of order (e.g. df_jk before df_build_B) */
+#define DF_E_NUMERIC (-6)    /* metric not positive definite, singular DIIS, NaN */
+#define DF_E_TIMEOUT (-7)    /* a device-side wait exceeded its iteration bound */
+
+#define DF_LMAX_ORB 2        /* orbital shells: s, p, d */
+#define DF_LMAX_AUX 3        /* auxiliary shells: s, p, d, f */
+
+typedef struct { double xyz[3]; int Z; } df_atom;
+
+/* One uncontracted shell. `center` is used as given (auxiliary shells may sit off the atoms);
+ * `atom` is informational. exponent > 0, 0 <= l <= DF_LMAX_ORB (orbital) / DF_LMAX_AUX (aux). */
+typedef struct { int atom; int l; double exponent; double center[3]; } df_shell;
+
+/* Precision of the K contraction (paper silent; the split form is this library's design). */
+#define DF_PREC_FP64 0       /* every step in FP64 */
+#define DF_PREC_SPLIT 1      /* K from split BF16 slices on tensor cores, FP32 accumulate, FP64 sum */
+
+#define DF_GUESS_CORE 0      /* core-Hamiltonian guess */
+
+typedef struct {
+    double conv_E;           /* |E_n - E_{n-1}| threshold (hartree), e.g. 1e-10 */
+    double conv_err;         /* max |X^T (F D S - S D F) X| threshold, e.g. 1e-7 */
+    int max_iter;            /* iteration cap */
+    int diis_size;           /* Pulay subspace (<= 16) */
+    int guess;               /* DF_GUESS_* */
+    int precision;           /* DF_PREC_* */
+    int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..4) */
+    int incremental;         /* 1: late iterations build K from the density change (split mode) */
+    double screen_tau;       /* drop shell triples whose bound is below tau (0 = none) */
+} df_options;
+
+typedef struct {
+    double energy;           /* total RHF energy */
+    double e_nuc;            /* nuclear repulsion */
+    double e_one;            /* tr(D H) */
+    double e_coul;           /* 1/2 tr(D J) */
+    double e_exch;           /* -1/2 tr(D K) */
+    double last_dE;
+    double last_err;
+    int iterations;
+    int converged;
+    int status;              /* DF_OK or DF_E_NOTCONV / DF_E_NUMERIC */
+    int n_dropped;           /* orbitals removed by canonical orthogonalisation */
+    double t_build_s;        /* df_build_B time within this call (0 if B was already built) */
+    double t_iter_s;         /* total SCF iteration time */
+    double t_jk_s;           /* time in J/K builds */
+    double t_total_s;
+} df_result;
+
+typedef struct df_handle df_handle;
+
+/* Create a handle: copies atoms and shells, validates them, uploads shell tables and computes the
+ * one-electron matrices S, T, V and the Coulomb metric (P|Q) on the GPU.
+ * natom >= 1; nbasis_sh, naux_sh >= 1; charge must leave an even electron count (closed shell).
+ * Returns DF_E_ARG for invalid shells (exponent <= 0, l out of range) or an odd electron count. */
+int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh,
+            const df_shell* aux, int naux_sh, int charge, df_handle** out);
+
+/* Sizes: n orbital functions, naux auxiliary functions, nocc doubly occupied orbitals, and the
+ * length of one packed row of B (doubles). Any pointer may be NULL. */
+int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed_row);
+
+/* Three-centre integrals (P|mu nu) per angular-momentum class, metric Cholesky (P|Q) = L L^T and
+ * whitening B = L^-1 (Q|mu nu), stored packed (mu >= nu tiles) and kept in HBM.
+ * Returns DF_E_NOMEM if the packed tensors do not fit; DF_E_NUMERIC if (P|Q) is not positive definite.
+ * screen_tau as in df_options (0 = compute every triple). keep_3c = 1 keeps the unwhitened tensor
+ * for df_get_rows (needs twice the memory). */
+int df_build_B(df_handle* h, double screen_tau, int keep_3c);
+
+/* Coulomb and exchange matrices for density D (n x n, symmetric) and occupied coefficients
+ * C_occ (n x nocc, row-major: C_occ[mu * nocc + i]):
+ *   J = sum_P gamma_P B_P with gamma_P = sum B_{P,mu nu} D_{mu nu};  K = sum_{P,i} Y Y^T.
+ * J and K are n x n outputs. device_ptrs = 1: all four are device pointers (on the handle's device);
+ * 0: host pointers, copied in and out inside the call. precision: DF_PREC_FP64 or DF_PREC_SPLIT
+ * (slices as in df_options). Requires df_build_B. */
+int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* J, double* K,
+          int device_ptrs, int precision, int slices);
+
+/* Full SCF from the core-Hamiltonian guess; builds B first if needed (screen_tau from opts).
+ * Results in *out; returns out->status. */
+int scf_run(df_handle* h, const df_options* opts, df_result* out);
+
+/* Copy rows [p0, p0+count) of an auxiliary-indexed tensor, unpacked to (count, n, n):
+ * which = 0: unwhitened (P|mu nu) (needs keep_3c), 1: whitened B. Host output. */
+int df_get_rows(df_handle* h, int which, int p0, int count, double* out);
+
+/* Copy a matrix to host: 0 S, 1 T, 2 V, 3 H, 4 metric (naux x naux), 5 L^-1 (naux x naux, lower),
+ * 6 D, 7 F, 8 J, 9 K (last SCF iteration), 10 C (n x n, columns = orbitals), 11 orbital energies (n). */
+int df_get_matrix(df_handle* h, int which, double* out);
+
+/* Rys quadrature nodes x (= t^2) and weights w for `count` arguments T (host arrays; x and w are
+ * count x nroots): the Gauss rule of exp(-T x) x^{-1/2} dx / 2 on [0,1], whose moments are the Boys
+ * functions, sum_i w_i x_i^k = F_k(T) for k < 2 nroots (paper, section "Molecular integrals": ERIs
+ * by Rys quadrature). A test hook for the device routine the integral kernels use. 1 <= nroots <= 4. */
+int df_rys(const double* T, int count, int nroots, double* x, double* w);
+
+/* Stream used by the handle (a cudaStream_t); NULL selects the handle's own stream. */
+int df_set_stream(df_handle* h, void* stream);
+
+/* Per-phase device times of the last df_build_B / df_jk in milliseconds (CUDA events):
+ * [0] 1e+metric, [1] three-centre ERI, [2] Cholesky+inverse, [3] whitening, [4] gamma, [5] J,
+ * [6] Y half-transform, [7] K contraction, [8] split slicing. Up to `count` values are written. */
+int df_timings(const df_handle* h, double* ms, int count);
+
+void df_free(df_handle* h);
+const char* df_strerror(int code);
+const char* df_last_error(const df_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFHF_H */

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libdfhf.so (include/dfhf.h): argument marshalling only.
+
+Every computation runs in the CUDA library; importing this module raises if the library has not
+been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, DF_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
+
+EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
+            "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error"]
+
+
+class Atom(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_double * 3), ("Z", ctypes.c_int)]
+
+
+class Shell(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("l", ctypes.c_int), ("exponent", ctypes.c_double),
+                ("center", ctypes.c_double * 3)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("conv_E", ctypes.c_double), ("conv_err", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("diis_size", ctypes.c_int), ("guess", ctypes.c_int), ("precision", ctypes.c_int),
+                ("slices", ctypes.c_int), ("incremental", ctypes.c_int), ("screen_tau", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("e_nuc", ctypes.c_double), ("e_one", ctypes.c_double),
+                ("e_coul", ctypes.c_double), ("e_exch", ctypes.c_double), ("last_dE", ctypes.c_double),
+                ("last_err", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("t_build_s", ctypes.c_double),
+                ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libdfhf.so (built by paper_1707_03771_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdfhf.so not built ({path}); run paper_1707_03771_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, c_int, c_double, c_void_p = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    dp = P(c_double)
+    L.df_init.argtypes = [P(Atom), c_int, P(Shell), c_int, P(Shell), c_int, c_int, P(c_void_p)]
+    L.df_sizes.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int), P(ctypes.c_longlong)]
+    L.df_build_B.argtypes = [c_void_p, c_double, c_int]
+    L.df_jk.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_int]
+    L.scf_run.argtypes = [c_void_p, P(Options), P(Result)]
+    L.df_get_rows.argtypes = [c_void_p, c_int, c_int, c_int, dp]
+    L.df_get_matrix.argtypes = [c_void_p, c_int, dp]
+    L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
+    L.df_set_stream.argtypes = [c_void_p, c_void_p]
+    L.df_timings.argtypes = [c_void_p, dp, c_int]
+    L.df_free.argtypes = [c_void_p]
+    L.df_free.restype = None
+    L.df_strerror.argtypes = [c_int]
+    L.df_strerror.restype = ctypes.c_char_p
+    L.df_last_error.argtypes = [c_void_p]
+    L.df_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+class DFError(RuntimeError):
+    def __init__(self, code, detail=""):
+        self.code = code
+        super().__init__(f"{load().df_strerror(code).decode()} ({code}) {detail}".strip())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _shells(arr):
+    out = (Shell * len(arr))()
+    for i, s in enumerate(arr):
+        out[i].atom = int(s["atom"])
+        out[i].l = int(s["l"])
+        out[i].exponent = float(s["exponent"])
+        out[i].center[:] = [float(x) for x in s["center"]]
+    return out
+
+
+def _atoms(arr):
+    out = (Atom * len(arr))()
+    for i, a in enumerate(arr):
+        out[i].xyz[:] = [float(x) for x in a["xyz"]]
+        out[i].Z = int(a["Z"])
+    return out
+
+
+MATRIX = {"S": 0, "T": 1, "V": 2, "H": 3, "metric": 4, "Linv": 5, "D": 6, "F": 7, "J": 8, "K": 9, "C": 10, "eps": 11}
+
+
+class Handle:
+    """One molecule on the GPU: wraps df_init ... df_free."""
+
+    def __init__(self, system):
+        L = load()
+        self.system = system
+        h = ctypes.c_void_p()
+        atoms, basis, aux = _atoms(system.atoms), _shells(system.basis), _shells(system.aux)
+        rc = L.df_init(atoms, len(system.atoms), basis, len(system.basis), aux, len(system.aux), int(system.charge),
+                       ctypes.byref(h))
+        if rc != DF_OK:
+            raise DFError(rc, "df_init")
+        self.h = h
+        n, na, no, row = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        L.df_sizes(h, ctypes.byref(n), ctypes.byref(na), ctypes.byref(no), ctypes.byref(row))
+        self.n, self.naux, self.nocc, self.packed_row = n.value, na.value, no.value, row.value
+
+    def _check(self, rc, what):
+        if rc != DF_OK:
+            raise DFError(rc, f"{what}: {load().df_last_error(self.h).decode()}")
+
+    def build_B(self, screen_tau: float = 0.0, keep_3c: bool = False):
+        self._check(load().df_build_B(self.h, screen_tau, int(keep_3c)), "df_build_B")
+
+    def jk(self, D, C_occ, precision=DF_PREC_FP64, slices=3):
+        """J, K for host arrays D (n x n) and C_occ (n x nocc); returns numpy arrays."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        C = np.ascontiguousarray(C_occ, dtype=np.float64)
+        J = np.empty((self.n, self.n))
+        K = np.empty((self.n, self.n))
+        rc = load().df_jk(self.h, D.ctypes.data, C.ctypes.data, C.shape[1], J.ctypes.data, K.ctypes.data, 0,
+                          precision, slices)
+        self._check(rc, "df_jk")
+        return J, K
+
+    def jk_device(self, D_ptr, C_ptr, nocc, J_ptr, K_ptr, precision=DF_PREC_FP64, slices=3):
+        """J, K with device pointers (e.g. torch tensors' data_ptr())."""
+        rc = load().df_jk(self.h, D_ptr, C_ptr, nocc, J_ptr, K_ptr, 1, precision, slices)
+        self._check(rc, "df_jk")
+
+    def scf(self, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
+            incremental=0, screen_tau=0.0):
+        o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau)
+        r = Result()
+        rc = load().scf_run(self.h, ctypes.byref(o), ctypes.byref(r))
+        if rc not in (DF_OK, DF_E_NOTCONV):
+            self._check(rc, "scf_run")
+        return r.as_dict()
+
+    def rows(self, which, p0, count):
+        out = np.empty((count, self.n, self.n))
+        self._check(load().df_get_rows(self.h, which, p0, count, _dp(out)), "df_get_rows")
+        return out
+
+    def matrix(self, name):
+        which = MATRIX[name]
+        if name in ("metric", "Linv"):
+            out = np.empty((self.naux, self.naux))
+        elif name == "eps":
+            out = np.empty(self.n)
+        else:
+            out = np.empty((self.n, self.n))
+        self._check(load().df_get_matrix(self.h, which, _dp(out)), f"df_get_matrix({name})")
+        return out
+
+    def timings(self):
+        out = np.zeros(16)
+        load().df_timings(self.h, _dp(out), 16)
+        keys = ["init_ms", "eri3c_ms", "cholesky_ms", "whiten_ms", "gamma_ms", "coulomb_ms", "ytransform_ms",
+                "kcontract_ms", "split_ms"]
+        return dict(zip(keys, out[:len(keys)]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().df_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def rys(T, nroots):
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    x = np.empty((len(T), nroots))
+    w = np.empty((len(T), nroots))
+    rc = load().df_rys(_dp(T), len(T), nroots, _dp(x), _dp(w))
+    if rc != DF_OK:
+        raise DFError(rc, "df_rys")
+    return x, w

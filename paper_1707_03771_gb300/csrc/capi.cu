@@ -1,0 +1,484 @@
+// The C ABI (include/dfhf.h): handle set-up, shell tables, B construction and the public entry
+// points. Every entry point converts internal exceptions into status codes.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace dfhf {
+
+void rys_eval(const double* dT, int count, int n, double* dx, double* dw, cudaStream_t s);
+
+namespace {
+
+// normalisation of N S_lm exp(-alpha r^2) with S_lm the real solid harmonics (norm independent of m):
+// int S_lm^2 exp(-2 alpha r^2) d^3r = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l+3/2})
+double shell_norm(int l, double alpha) {
+    double dfact = 1.0;
+    for (int k = 2 * l - 1; k > 1; k -= 2) dfact *= k;
+    const double pi = 3.14159265358979323846;
+    const double integral = std::pow(pi, 1.5) * dfact / (std::pow(2.0, l) * std::pow(2.0 * alpha, l + 1.5));
+    return 1.0 / std::sqrt(integral);
+}
+
+void upload_shells(const std::vector<df_shell>& sh, ShellTable& t, cudaStream_t s) {
+    const int n = (int)sh.size();
+    std::vector<int> l(n), off(n);
+    std::vector<double> a(n), nrm(n), xyz(3 * n);
+    int o = 0;
+    for (int i = 0; i < n; ++i) {
+        l[i] = sh[i].l;
+        off[i] = o;
+        o += 2 * sh[i].l + 1;
+        a[i] = sh[i].exponent;
+        nrm[i] = shell_norm(sh[i].l, sh[i].exponent);
+        for (int d = 0; d < 3; ++d) xyz[3 * i + d] = sh[i].center[d];
+    }
+    t.count = n;
+    DF_CUDA(cudaMalloc((void**)&t.l, sizeof(int) * n));
+    DF_CUDA(cudaMalloc((void**)&t.off, sizeof(int) * n));
+    DF_CUDA(cudaMalloc((void**)&t.alpha, sizeof(double) * n));
+    DF_CUDA(cudaMalloc((void**)&t.norm, sizeof(double) * n));
+    DF_CUDA(cudaMalloc((void**)&t.xyz, sizeof(double) * 3 * n));
+    DF_CUDA(cudaMemcpyAsync(t.l, l.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(t.off, off.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(t.alpha, a.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(t.norm, nrm.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(t.xyz, xyz.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaStreamSynchronize(s));
+}
+
+void free_shells(ShellTable& t) {
+    cudaFree(t.l);
+    cudaFree(t.off);
+    cudaFree(t.alpha);
+    cudaFree(t.norm);
+    cudaFree(t.xyz);
+    t = ShellTable{};
+}
+
+// shell pairs (M >= N) grouped by class (la >= lb), the higher l first in each pair
+std::vector<ClassList> make_pairs(const std::vector<df_shell>& sh, int lmax, cudaStream_t s) {
+    std::vector<std::vector<int2>> buckets((lmax + 1) * (lmax + 1));
+    for (int M = 0; M < (int)sh.size(); ++M)
+        for (int N = 0; N <= M; ++N) {
+            int a = M, b = N;
+            if (sh[a].l < sh[b].l) std::swap(a, b);
+            buckets[sh[a].l * (lmax + 1) + sh[b].l].push_back(make_int2(a, b));
+        }
+    std::vector<ClassList> out;
+    for (int la = 0; la <= lmax; ++la)
+        for (int lb = 0; lb <= la; ++lb) {
+            auto& v = buckets[la * (lmax + 1) + lb];
+            ClassList c;
+            c.la = la;
+            c.lb = lb;
+            c.count = (int)v.size();
+            if (c.count) {
+                DF_CUDA(cudaMalloc((void**)&c.d_pairs, sizeof(int2) * c.count));
+                DF_CUDA(cudaMemcpyAsync(c.d_pairs, v.data(), sizeof(int2) * c.count, cudaMemcpyHostToDevice, s));
+            }
+            out.push_back(c);
+        }
+    DF_CUDA(cudaStreamSynchronize(s));
+    return out;
+}
+
+__global__ void add_kernel(const double* a, const double* b, long long n, double* c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] + b[i];
+}
+
+// zero the strictly upper triangle of a row-major square matrix
+__global__ void zero_upper_kernel(double* M, int n) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    if (idx % n > idx / n) M[idx] = 0.0;
+}
+
+int fail(df_handle* h, const Error& e) {
+    if (h) h->last_error = e.msg;
+    return e.code;
+}
+
+}  // namespace
+
+void build_B(df_handle* h, double tau, bool keep) {
+    cudaStream_t s = h->stream;
+    const size_t rows = (size_t)h->naux * h->pk.row;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
+    h->B.release();
+    h->A3c.release();
+    h->A3c.alloc(rows);
+    DF_CUDA(cudaEventRecord(ev[0], s));
+    compute_three_center(h, h->A3c.p, tau);
+    DF_CUDA(cudaEventRecord(ev[1], s));
+    // metric Cholesky (P|Q) = L L^T: cuSOLVER works column-major, so the upper factor U (V = U^T U)
+    // of the column-major matrix is the row-major lower factor L = U^T; likewise trtri of U gives L^-1.
+    const int na = h->naux;
+    h->Linv.alloc((size_t)na * na);
+    DF_CUDA(cudaMemcpyAsync(h->Linv.p, h->metric.p, sizeof(double) * na * na, cudaMemcpyDeviceToDevice, s));
+    int lwork = 0;
+    DF_SOLVER(cusolverDnDpotrf_bufferSize(h->solver, CUBLAS_FILL_MODE_UPPER, na, h->Linv.p, na, &lwork));
+    double* work = nullptr;
+    int* info = nullptr;
+    DF_CUDA(cudaMalloc((void**)&work, sizeof(double) * std::max(lwork, 1)));
+    DF_CUDA(cudaMalloc((void**)&info, sizeof(int)));
+    int hinfo = 0;
+    try {
+        DF_SOLVER(cusolverDnDpotrf(h->solver, CUBLAS_FILL_MODE_UPPER, na, h->Linv.p, na, work, lwork, info));
+        DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DF_CUDA(cudaStreamSynchronize(s));
+        if (hinfo != 0) throw Error{DF_E_NUMERIC, "metric (P|Q) is not positive definite (potrf info " + std::to_string(hinfo) + ")"};
+        size_t dws = 0, hws = 0;
+        DF_SOLVER(cusolverDnXtrtri_bufferSize(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
+                                              h->Linv.p, na, &dws, &hws));
+        void* dbuf = nullptr;
+        std::vector<char> hbuf(std::max<size_t>(hws, 1));
+        DF_CUDA(cudaMalloc(&dbuf, std::max<size_t>(dws, 1)));
+        cusolverStatus_t st = cusolverDnXtrtri(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
+                                               h->Linv.p, na, dbuf, dws, hbuf.data(), hws, info);
+        DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DF_CUDA(cudaStreamSynchronize(s));
+        cudaFree(dbuf);
+        if (st != CUSOLVER_STATUS_SUCCESS) throw Error{DF_E_CUDA, "cusolverDnXtrtri failed"};
+        if (hinfo != 0) throw Error{DF_E_NUMERIC, "metric Cholesky factor is singular"};
+    } catch (...) {
+        cudaFree(work);
+        cudaFree(info);
+        throw;
+    }
+    cudaFree(work);
+    cudaFree(info);
+    zero_upper_kernel<<<(unsigned)(((long long)na * na + 255) / 256), 256, 0, s>>>(h->Linv.p, na);
+    DF_CHECK_LAUNCH();
+    DF_CUDA(cudaEventRecord(ev[2], s));
+    h->B.alloc(rows);
+    dtrmm_lower(s, na, h->pk.row, h->Linv.p, h->A3c.p, h->B.p, h->pk.row);
+    DF_CUDA(cudaEventRecord(ev[3], s));
+    DF_CUDA(cudaEventSynchronize(ev[3]));
+    h->timings_ms[1] = elapsed_ms(ev[0], ev[1]);
+    h->timings_ms[2] = elapsed_ms(ev[1], ev[2]);
+    h->timings_ms[3] = elapsed_ms(ev[2], ev[3]);
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (!keep) h->A3c.release();
+    h->built = true;
+}
+
+void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
+                 int slices) {
+    ensure_jk_buffers(h, nocc);
+    coulomb_fp64(h, dD, dJ);
+    const int ldy = ((nocc + 31) / 32) * 32;
+    pad_occupied(h, dC, nocc, ldy);
+    if (precision == DF_PREC_SPLIT)
+        exchange_split(h, nocc, slices, dK);
+    else
+        exchange_fp64(h, nocc, dK);
+}
+
+}  // namespace dfhf
+
+using namespace dfhf;
+
+extern "C" {
+
+const char* df_strerror(int code) {
+    switch (code) {
+        case DF_OK: return "ok";
+        case DF_E_ARG: return "invalid argument";
+        case DF_E_NOMEM: return "device memory exhausted";
+        case DF_E_CUDA: return "CUDA or cuSOLVER error";
+        case DF_E_NOTCONV: return "SCF did not converge";
+        case DF_E_STATE: return "call out of order";
+        case DF_E_NUMERIC: return "numerical failure";
+        case DF_E_TIMEOUT: return "device wait timed out";
+        default: return "unknown error";
+    }
+}
+
+const char* df_last_error(const df_handle* h) { return h ? h->last_error.c_str() : ""; }
+
+int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh, const df_shell* aux, int naux_sh,
+            int charge, df_handle** out) {
+    if (!out) return DF_E_ARG;
+    *out = nullptr;
+    if (!atoms || !basis || !aux || natom < 1 || nbasis_sh < 1 || naux_sh < 1) return DF_E_ARG;
+    for (int i = 0; i < nbasis_sh; ++i)
+        if (!(basis[i].exponent > 0) || basis[i].l < 0 || basis[i].l > DF_LMAX_ORB) return DF_E_ARG;
+    for (int i = 0; i < naux_sh; ++i)
+        if (!(aux[i].exponent > 0) || aux[i].l < 0 || aux[i].l > DF_LMAX_AUX) return DF_E_ARG;
+    int zsum = 0;
+    for (int i = 0; i < natom; ++i) {
+        if (atoms[i].Z < 0) return DF_E_ARG;
+        zsum += atoms[i].Z;
+    }
+    const int nelec = zsum - charge;
+    if (nelec < 2 || nelec % 2) return DF_E_ARG;
+    df_handle* h = new (std::nothrow) df_handle();
+    if (!h) return DF_E_NOMEM;
+    try {
+        DF_CUDA(cudaGetDevice(&h->device));
+        DF_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        h->stream = h->own_stream;
+        DF_SOLVER(cusolverDnCreate(&h->solver));
+        DF_SOLVER(cusolverDnSetStream(h->solver, h->stream));
+        h->atoms.assign(atoms, atoms + natom);
+        h->basis.assign(basis, basis + nbasis_sh);
+        h->aux.assign(aux, aux + naux_sh);
+        for (auto& s : h->basis) h->n += 2 * s.l + 1;
+        for (auto& s : h->aux) h->naux += 2 * s.l + 1;
+        h->nelec = nelec;
+        h->nocc = nelec / 2;
+        if (h->nocc > h->n) throw Error{DF_E_ARG, "more occupied orbitals than basis functions"};
+        for (int i = 0; i < natom; ++i)
+            for (int j = 0; j < i; ++j) {
+                double r2 = 0;
+                for (int d = 0; d < 3; ++d) r2 += (atoms[i].xyz[d] - atoms[j].xyz[d]) * (atoms[i].xyz[d] - atoms[j].xyz[d]);
+                if (r2 == 0 && atoms[i].Z * atoms[j].Z != 0) throw Error{DF_E_ARG, "coincident nuclei"};
+                if (r2 > 0) h->e_nuc += atoms[i].Z * atoms[j].Z / std::sqrt(r2);
+            }
+        Packing& pk = h->pk;
+        pk.n = h->n;
+        pk.nt = (h->n + TS - 1) / TS;
+        pk.np = pk.nt * TS;
+        pk.ntp = (long long)pk.nt * (pk.nt + 1) / 2;
+        pk.row = pk.ntp * TS * TS;
+        cudaStream_t s = h->stream;
+        upload_shells(h->basis, h->dbas, s);
+        upload_shells(h->aux, h->daux, s);
+        h->pair_classes = make_pairs(h->basis, DF_LMAX_ORB, s);
+        h->aux_pairs = make_pairs(h->aux, DF_LMAX_AUX, s);
+        h->aux_by_l.assign(DF_LMAX_AUX + 1, {});
+        for (int i = 0; i < naux_sh; ++i) h->aux_by_l[h->aux[i].l].push_back(i);
+        for (int l = 0; l <= DF_LMAX_AUX; ++l)
+            if (!h->aux_by_l[l].empty()) {
+                h->d_aux_by_l[l].alloc(h->aux_by_l[l].size());
+                DF_CUDA(cudaMemcpyAsync(h->d_aux_by_l[l].p, h->aux_by_l[l].data(), sizeof(int) * h->aux_by_l[l].size(),
+                                        cudaMemcpyHostToDevice, s));
+            }
+        std::vector<double> axyz(3 * natom), aZ(natom);
+        for (int i = 0; i < natom; ++i) {
+            aZ[i] = atoms[i].Z;
+            for (int d = 0; d < 3; ++d) axyz[3 * i + d] = atoms[i].xyz[d];
+        }
+        h->d_atom_xyz.alloc(3 * natom);
+        h->d_atom_Z.alloc(natom);
+        DF_CUDA(cudaMemcpyAsync(h->d_atom_xyz.p, axyz.data(), sizeof(double) * 3 * natom, cudaMemcpyHostToDevice, s));
+        DF_CUDA(cudaMemcpyAsync(h->d_atom_Z.p, aZ.data(), sizeof(double) * natom, cudaMemcpyHostToDevice, s));
+        const size_t nn = (size_t)h->n * h->n;
+        h->S.alloc(nn);
+        h->T.alloc(nn);
+        h->V.alloc(nn);
+        h->H.alloc(nn);
+        h->metric.alloc((size_t)h->naux * h->naux);
+        cudaEvent_t e0, e1;
+        DF_CUDA(cudaEventCreate(&e0));
+        DF_CUDA(cudaEventCreate(&e1));
+        DF_CUDA(cudaEventRecord(e0, s));
+        compute_one_electron(h);
+        add_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(h->T.p, h->V.p, (long long)nn, h->H.p);
+        DF_CHECK_LAUNCH();
+        compute_metric(h);
+        DF_CUDA(cudaEventRecord(e1, s));
+        DF_CUDA(cudaEventSynchronize(e1));
+        h->timings_ms[0] = elapsed_ms(e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    } catch (const Error& e) {
+        int code = e.code;
+        df_free(h);
+        return code;
+    } catch (const std::bad_alloc&) {
+        df_free(h);
+        return DF_E_NOMEM;
+    }
+    *out = h;
+    return DF_OK;
+}
+
+int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed_row) {
+    if (!h) return DF_E_ARG;
+    if (n) *n = h->n;
+    if (naux) *naux = h->naux;
+    if (nocc) *nocc = h->nocc;
+    if (packed_row) *packed_row = h->pk.row;
+    return DF_OK;
+}
+
+int df_build_B(df_handle* h, double screen_tau, int keep_3c) {
+    if (!h || screen_tau < 0) return DF_E_ARG;
+    try {
+        DF_CUDA(cudaSetDevice(h->device));
+        build_B(h, screen_tau, keep_3c != 0);
+    } catch (const Error& e) {
+        h->B.release();
+        h->A3c.release();
+        h->built = false;
+        return fail(h, e);
+    }
+    return DF_OK;
+}
+
+int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* J, double* K, int device_ptrs,
+          int precision, int slices) {
+    if (!h || !D || !C_occ || !J || !K || nocc < 1 || nocc > h->n) return DF_E_ARG;
+    if (precision != DF_PREC_FP64 && precision != DF_PREC_SPLIT) return DF_E_ARG;
+    if (precision == DF_PREC_SPLIT && (slices < 2 || slices > 4)) return DF_E_ARG;
+    if (!h->built) return fail(h, Error{DF_E_STATE, "df_jk before df_build_B"});
+    try {
+        DF_CUDA(cudaSetDevice(h->device));
+        ensure_jk_buffers(h, nocc);
+        const size_t nn = (size_t)h->n * h->n;
+        cudaStream_t s = h->stream;
+        const double *dD = D, *dC = C_occ;
+        double *dJ = J, *dK = K;
+        if (!device_ptrs) {
+            DF_CUDA(cudaMemcpyAsync(h->dD.p, D, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+            DF_CUDA(cudaMemcpyAsync(h->dC.p, C_occ, (size_t)h->n * nocc * sizeof(double), cudaMemcpyHostToDevice, s));
+            dD = h->dD.p;
+            dC = h->dC.p;
+            dJ = h->dJ.p;
+            dK = h->dK.p;
+        }
+        jk_dispatch(h, dD, dC, nocc, dJ, dK, precision, slices);
+        if (!device_ptrs) {
+            DF_CUDA(cudaMemcpyAsync(J, dJ, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+            DF_CUDA(cudaMemcpyAsync(K, dK, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        DF_CUDA(cudaStreamSynchronize(s));
+    } catch (const Error& e) {
+        return fail(h, e);
+    }
+    return DF_OK;
+}
+
+int scf_run(df_handle* h, const df_options* opts, df_result* out) {
+    if (!h || !opts || !out) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
+    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 4)) return DF_E_ARG;
+    try {
+        DF_CUDA(cudaSetDevice(h->device));
+        return scf_drive(h, opts, out);
+    } catch (const Error& e) {
+        out->status = e.code;
+        return fail(h, e);
+    }
+}
+
+int df_get_rows(df_handle* h, int which, int p0, int count, double* out) {
+    if (!h || !out || p0 < 0 || count < 1 || p0 + count > h->naux || (which != 0 && which != 1)) return DF_E_ARG;
+    const double* src = which == 0 ? h->A3c.p : h->B.p;
+    if (!src) return fail(h, Error{DF_E_STATE, which == 0 ? "unwhitened tensor not kept" : "B not built"});
+    try {
+        const size_t nn = (size_t)h->n * h->n;
+        DevBuf<double> tmp;
+        tmp.alloc(nn * count);
+        unpack_rows(h, src, p0, count, tmp.p);
+        DF_CUDA(cudaMemcpyAsync(out, tmp.p, nn * count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        DF_CUDA(cudaStreamSynchronize(h->stream));
+        tmp.release();
+    } catch (const Error& e) {
+        return fail(h, e);
+    }
+    return DF_OK;
+}
+
+int df_get_matrix(df_handle* h, int which, double* out) {
+    if (!h || !out) return DF_E_ARG;
+    const size_t nn = (size_t)h->n * h->n, aa = (size_t)h->naux * h->naux;
+    const double* src = nullptr;
+    size_t count = nn;
+    switch (which) {
+        case 0: src = h->S.p; break;
+        case 1: src = h->T.p; break;
+        case 2: src = h->V.p; break;
+        case 3: src = h->H.p; break;
+        case 4: src = h->metric.p; count = aa; break;
+        case 5: src = h->Linv.p; count = aa; break;
+        case 6: src = h->Dm.p; break;
+        case 7: src = h->F.p; break;
+        case 8: src = h->dJ.p; break;
+        case 9: src = h->dK.p; break;
+        case 10: src = h->C.p; count = (size_t)h->n * h->nX; break;
+        case 11: src = h->eps.p; count = h->n; break;
+        default: return DF_E_ARG;
+    }
+    if (!src) return fail(h, Error{DF_E_STATE, "matrix not available yet"});
+    try {
+        if (which == 10 && h->nX < h->n) {   // pad dropped orbitals with zero columns
+            std::vector<double> tmp((size_t)h->n * h->nX);
+            DF_CUDA(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int r = 0; r < h->n; ++r)
+                for (int c = 0; c < h->n; ++c) out[(size_t)r * h->n + c] = c < h->nX ? tmp[(size_t)r * h->nX + c] : 0.0;
+            return DF_OK;
+        }
+        DF_CUDA(cudaStreamSynchronize(h->stream));
+        DF_CUDA(cudaMemcpy(out, src, count * sizeof(double), cudaMemcpyDeviceToHost));
+    } catch (const Error& e) {
+        return fail(h, e);
+    }
+    return DF_OK;
+}
+
+int df_rys(const double* T, int count, int nroots, double* x, double* w) {
+    if (!T || !x || !w || count < 1 || nroots < 1 || nroots > 4) return DF_E_ARG;
+    try {
+        double *dT = nullptr, *dx = nullptr, *dw = nullptr;
+        DF_CUDA(cudaMalloc((void**)&dT, sizeof(double) * count));
+        DF_CUDA(cudaMalloc((void**)&dx, sizeof(double) * count * nroots));
+        DF_CUDA(cudaMalloc((void**)&dw, sizeof(double) * count * nroots));
+        DF_CUDA(cudaMemcpy(dT, T, sizeof(double) * count, cudaMemcpyHostToDevice));
+        rys_eval(dT, count, nroots, dx, dw, 0);
+        DF_CUDA(cudaMemcpy(x, dx, sizeof(double) * count * nroots, cudaMemcpyDeviceToHost));
+        DF_CUDA(cudaMemcpy(w, dw, sizeof(double) * count * nroots, cudaMemcpyDeviceToHost));
+        cudaFree(dT);
+        cudaFree(dx);
+        cudaFree(dw);
+    } catch (const Error& e) {
+        return e.code;
+    }
+    return DF_OK;
+}
+
+int df_set_stream(df_handle* h, void* stream) {
+    if (!h) return DF_E_ARG;
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    if (cusolverDnSetStream(h->solver, h->stream) != CUSOLVER_STATUS_SUCCESS) return DF_E_CUDA;
+    return DF_OK;
+}
+
+int df_timings(const df_handle* h, double* ms, int count) {
+    if (!h || !ms || count < 0) return DF_E_ARG;
+    for (int i = 0; i < count && i < 16; ++i) ms[i] = h->timings_ms[i];
+    return DF_OK;
+}
+
+void df_free(df_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_split(h);
+    free_shells(h->dbas);
+    free_shells(h->daux);
+    for (auto& c : h->pair_classes) cudaFree(c.d_pairs);
+    for (auto& c : h->aux_pairs) cudaFree(c.d_pairs);
+    if (h->solver) cusolverDnDestroy(h->solver);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    // DevBuf members are released explicitly (they have no destructor so a copy cannot double free)
+    DevBuf<double>* bufs[] = {&h->d_atom_xyz, &h->d_atom_Z, &h->S, &h->T, &h->V, &h->H, &h->metric, &h->Linv,
+                              &h->A3c, &h->B, &h->Dw, &h->gamma, &h->Jp, &h->Y, &h->Kpart, &h->Cpad, &h->dD,
+                              &h->dC, &h->dJ, &h->dK, &h->X, &h->F, &h->Fx, &h->Dm, &h->C, &h->eps, &h->work1,
+                              &h->work2, &h->work3, &h->diisF, &h->diisE, &h->diisB};
+    for (auto* b : bufs) b->release();
+    h->ktiles.release();
+    for (auto& b : h->d_aux_by_l) b.release();
+    delete h;
+}
+
+}  // extern "C"
