@@ -1,0 +1,341 @@
+"""Benchmark of the density-fitted RHF hot path on GB300.
+
+Workload: a seeded 32-water cluster (1600 basis functions, 4384 auxiliary functions, 160 occupied
+orbitals, packed whitened B of 46.7 GB resident in HBM), synthetic geometry and even-tempered bases.
+
+A step is one density-fitted Fock build from the resident B: gamma = B.D, J = B^T gamma, the
+half-transform Y = B C_occ and K = sum_P Y_P Y_P^T (paper eqs. 1-3). `value` is seconds per J/K
+build with inputs already on the device (CUDA events on the library's stream, max over ranks);
+`e2e` is the same through the C ABI with host buffers (D and C_occ copied in, J and K copied out
+inside the timed region). `time_to_converge_s` is one full SCF (integrals + whitening + iterations)
+from the core-Hamiltonian guess to |dE| < 1e-10 Eh.
+
+Inputs (46.7 GB of B) are far larger than L2 (126 MB), so no flush is needed between steps.
+Under torchrun with N > 1 each rank runs an independent replica (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "water32"
+METRIC = "SCF time-to-converge & DF J/K s/iter: split-prec+batched+learned vs FP64"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 DFMA peak of GB300 measured with a dependent-chain-free DFMA loop over all 152 SMs
+# (1.00 TFLOP/s; DMMA m8n8k4 gave 1.05 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.00
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1707_03771_gb300 import binding, build, clusters
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or ws > 1:
+        build.build()
+    if ws > 1:
+        tdist.barrier()
+    lib = binding.load()
+    system = clusters.workload(args.workload)
+    precision = binding.DF_PREC_SPLIT if args.precision == "split" else binding.DF_PREC_FP64
+
+    t0 = time.perf_counter()
+    h = binding.Handle(system)
+    h.build_B()
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    build_ms = h.timings()
+
+    # a physical density for the timed builds: the core-Hamiltonian orbitals
+    n, nocc = h.n, h.nocc
+    S, H = h.matrix("S"), h.matrix("H")
+    s, U = np.linalg.eigh(S)
+    X = U[:, s > 1e-7] / np.sqrt(s[s > 1e-7])
+    e, Cp = np.linalg.eigh(X.T @ H @ X)
+    C = np.ascontiguousarray((X @ Cp)[:, :nocc])
+    D = 2 * C @ C.T
+    dev = torch.device("cuda", local)
+    dD = torch.from_numpy(D).to(dev)
+    dC = torch.from_numpy(C).to(dev)
+    dJ = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dK = torch.empty((n, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
+
+    def step():
+        h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, args.slices)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        tdist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dom_ms = []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            dom_ms.append(dict(h.timings()))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C ABI with host buffers
+    Jh = np.empty((n, n))
+    Kh = np.empty((n, n))
+    lib.df_set_stream(h.h, None)
+    for _ in range(2):
+        h.jk(D, C, precision, args.slices)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        Jh, Kh = h.jk(D, C, precision, args.slices)
+    e2e_s = (time.perf_counter() - t1) / args.steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # time to a converged SCF (B already built: add the build time measured above)
+    ttc = None
+    scf_info = None
+    if args.ttc:
+        res = h.scf(precision=precision, slices=args.slices)
+        ttc = t_build + res["t_total_s"]
+        scf_info = {"energy": res["energy"], "iterations": res["iterations"], "converged": bool(res["converged"]),
+                    "t_iter_s": res["t_iter_s"], "t_jk_s": res["t_jk_s"]}
+
+    # roofline of the dominant kernel
+    peaks, peak_src = _peaks()
+    keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms"]
+    avg = {k: float(np.mean([d[k] for d in dom_ms])) for k in keys}
+    naux, npair = h.naux, n * (n + 1) // 2
+    if precision == binding.DF_PREC_FP64:
+        dom = "ytransform_ms"
+        flops = 2.0 * naux * n * n * nocc          # Y = B C: 2 naux n^2 nocc
+        achieved = flops / (avg[dom] * 1e-3) / 1e12
+        roofline = {"kernel": "y_transform_kernel (FP64 DFMA)", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "measured FP64 DFMA loop (not in MEASURED_PEAKS.json)", "traffic": None}
+    else:
+        dom = "kcontract_ms"
+        hw_flops = float(os.environ.get("DF_SPLIT_HW_FLOPS", "0"))
+        achieved = hw_flops / (avg[dom] * 1e-3) / 1e12 if hw_flops else None
+        pk = peaks.get("bf16_tflops")
+        roofline = {"kernel": "split K contraction (BF16 tensor cores)", "bound": "tensor", "achieved": achieved,
+                    "peak": pk, "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None,
+                    "peak_source": peak_src, "traffic": None}
+    kernel_ms = {k: round(v, 3) for k, v in avg.items()}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(system, budget_s=args.cpu_budget)
+
+    line = {
+        "metric": METRIC, "value": ms_per_step / 1000.0, "unit": "s/iter (DF J+K build)",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == binding.DF_PREC_FP64 else f"bf16x{args.slices}-split/f32acc/f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: seeded water cluster, n={n}, naux={naux}, nocc={nocc}, "
+                               f"packed B {h.naux * h.packed_row * 8 / 1e9:.1f} GB",
+                   "precision": args.precision, "l2": "inputs larger than L2 (B resident, no flush)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": e2e_s, "unit": "s/iter (DF J+K build, host buffers)",
+                "h2d_bytes_per_step": int(D.nbytes + C.nbytes), "d2h_bytes_per_step": int(Jh.nbytes + Kh.nbytes)},
+        "gpu_launches": args.steps * launches_per_step(precision),
+        "roofline": roofline,
+        "kernel_ms": kernel_ms,
+        "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
+                    "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
+                    "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
+        "time_to_converge_s": ttc, "scf": scf_info,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+def ctypes_ptr(v):
+    import ctypes
+    return ctypes.c_void_p(v)
+
+
+def launches_per_step(precision):
+    # pack D, gamma, coulomb, split-sum, unpack J, pad C, Y transform, K contraction, K reduce
+    return 9 if precision == 0 else 9 + 2
+
+
+def _oracle_jk_sample(system, rows, rng):
+    """Oracle J/K (eqs. 1-3) on `rows` auxiliary rows of a synthetic B with the workload's shape."""
+    from oracle import dfrhf
+    n, nocc = system.nbf, system.nocc
+    B = rng.standard_normal((rows, n, n))
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    C = rng.standard_normal((n, nocc))
+    D = 2 * C @ C.T
+    t0 = time.perf_counter()
+    dfrhf.df_J(B, D)
+    dfrhf.df_K(B, C)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(system, budget_s=15.0):
+    """The oracle's J/K contraction (numpy, as it stands) on a bounded sample of auxiliary rows,
+    scaled linearly to all naux rows (the cost of eqs. 1-3 is linear in naux)."""
+    rng = np.random.default_rng(0)
+    rows = 2
+    t = _oracle_jk_sample(system, rows, rng)
+    while t < budget_s / 4 and rows < 64:
+        rows *= 2
+        t = _oracle_jk_sample(system, rows, rng)
+    per_iter = t / rows * system.naux
+    try:
+        import numpy.__config__  # noqa: F401
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    except Exception:
+        threads = os.cpu_count()
+    return {"value": per_iter, "unit": "s/iter (DF J+K build)", "cores": threads, "kind": "oracle",
+            "sample": f"oracle df_J + df_K on {rows} of {system.naux} auxiliary rows "
+                      f"(n={system.nbf}, nocc={system.nocc}), {t:.1f} s, scaled by naux/{rows}"}
+
+
+def reference_arm(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from paper_1707_03771_gb300 import clusters
+    system = clusters.workload(args.workload)
+    rng = np.random.default_rng(1)
+    rows = 4
+    for _ in range(args.warmup):
+        _oracle_jk_sample(system, rows, rng)
+    times = [_oracle_jk_sample(system, rows, rng) / rows * system.naux for _ in range(args.steps)]
+    v = float(np.mean(times))
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": v, "unit": "s/iter (DF J+K build)", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1000, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: seeded water cluster, n={system.nbf}, naux={system.naux}, "
+                                   f"nocc={system.nocc}", "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": "s/iter (DF J+K build)", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle df_J + df_K on {rows} of {system.naux} auxiliary rows per step, "
+                                       f"scaled by naux/{rows}"},
+            "e2e": {"value": v, "unit": "s/iter (DF J+K build)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default=os.environ.get("DF_BENCH_PRECISION", "fp64"), choices=["fp64", "split"])
+    ap.add_argument("--slices", type=int, default=3)
+    ap.add_argument("--no-ttc", dest="ttc", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -135,6 +135,11 @@ int df_get_matrix(df_handle* h, int which, double* out);
  * by Rys quadrature). A test hook for the device routine the integral kernels use. 1 <= nroots <= 4. */
 int df_rys(const double* T, int count, int nroots, double* x, double* w);
 
+/* Host-side set-up without a GPU: builds and validates the Rys root/weight table (Gauss rules of the
+ * Boys-function measure) and caches it as rys_table.bin beside the library (or at $DFHF_TABLE_CACHE).
+ * Optional: the first integral call does the same. Returns DF_E_NUMERIC if the table fails its check. */
+int df_prepare(void);
+
 /* Stream used by the handle (a cudaStream_t); NULL selects the handle's own stream. */
 int df_set_stream(df_handle* h, void* stream);
 

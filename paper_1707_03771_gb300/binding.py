@@ -16,7 +16,7 @@ DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, 
 DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
-            "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error"]
+            "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error"]
 
 
 class Atom(ctypes.Structure):
@@ -71,6 +71,7 @@ def load(path: str | None = None):
     L.df_get_rows.argtypes = [c_void_p, c_int, c_int, c_int, dp]
     L.df_get_matrix.argtypes = [c_void_p, c_int, dp]
     L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
+    L.df_prepare.argtypes = []
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]

@@ -67,7 +67,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
     os.replace(tmp, LIB)
+    prepare()
     return LIB
+
+
+def prepare() -> None:
+    """Build and cache the host-side Rys table next to the library (no GPU needed)."""
+    import ctypes
+    rc = ctypes.CDLL(LIB).df_prepare()
+    if rc != 0:
+        raise RuntimeError(f"df_prepare failed with status {rc}")
 
 
 if __name__ == "__main__":

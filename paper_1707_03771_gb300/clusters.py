@@ -184,6 +184,8 @@ def water_cluster(n_water: int, seed: int) -> System:
 # Named workloads (sizes in functions: orbital n, auxiliary naux, occupied nocc).
 WORKLOADS = {
     "water2": dict(n_water=2, seed=0),     # n=100,  naux=274,  nocc=10
+    "water8": dict(n_water=8, seed=8),     # n=400,  naux=1096, nocc=40
+    "water16": dict(n_water=16, seed=16),  # n=800,  naux=2192, nocc=80
     "water32": dict(n_water=32, seed=1),   # n=1600, naux=4384, nocc=160
     "water40": dict(n_water=40, seed=2),   # n=2000, naux=5480, nocc=200
 }

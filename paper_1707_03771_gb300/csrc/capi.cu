@@ -11,6 +11,7 @@
 namespace dfhf {
 
 void rys_eval(const double* dT, int count, int n, double* dx, double* dw, cudaStream_t s);
+const double* rys_table_host();
 
 namespace {
 
@@ -440,6 +441,15 @@ int df_rys(const double* T, int count, int nroots, double* x, double* w) {
         cudaFree(dT);
         cudaFree(dx);
         cudaFree(dw);
+    } catch (const Error& e) {
+        return e.code;
+    }
+    return DF_OK;
+}
+
+int df_prepare(void) {
+    try {
+        rys_table_host();
     } catch (const Error& e) {
         return e.code;
     }

@@ -12,12 +12,18 @@
 // intervals of T, and the fit is checked against the directly computed moments before use.
 // For T >= 60 the rule is generalised Gauss-Laguerre with alpha = -1/2 (monic recurrence
 // alpha_k = 2k + 1/2, beta_k = k (k - 1/2), beta_0 = Gamma(1/2)).
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <unistd.h>
 
 #include "common.cuh"
 #include "rys.cuh"
@@ -226,11 +232,70 @@ std::mutex g_mu;
 std::vector<double> g_host;
 std::map<int, double*> g_dev;
 
+// The table takes seconds to build where long double is emulated in software, so the validated
+// table is cached beside the library: 8-byte magic, entry count, the doubles, FNV-1a of their bytes.
+const char kMagic[8] = {'D', 'F', 'R', 'Y', 'S', '0', '0', '1'};
+
+uint64_t fnv1a(const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    uint64_t h = 1469598103934665603ULL;
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+    return h;
+}
+
+std::string cache_path() {
+    if (const char* env = std::getenv("DFHF_TABLE_CACHE")) return env;
+    Dl_info info;
+    if (dladdr((void*)&fnv1a, &info) && info.dli_fname) {
+        std::string f = info.dli_fname;
+        size_t slash = f.rfind('/');
+        return (slash == std::string::npos ? std::string(".") : f.substr(0, slash)) + "/rys_table.bin";
+    }
+    return "";
+}
+
+bool load_cache(const std::string& path, std::vector<double>& out) {
+    if (path.empty()) return false;
+    FILE* f = std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    char magic[8];
+    long long count = 0;
+    uint64_t sum = 0;
+    std::vector<double> v(RYS_TABLE_SIZE);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&count, sizeof(count), 1, f) == 1 && count == RYS_TABLE_SIZE &&
+              std::fread(v.data(), sizeof(double), v.size(), f) == v.size() && std::fread(&sum, sizeof(sum), 1, f) == 1 &&
+              sum == fnv1a(v.data(), v.size() * sizeof(double));
+    std::fclose(f);
+    if (ok) out.swap(v);
+    return ok;
+}
+
+void store_cache(const std::string& path, const std::vector<double>& v) {
+    if (path.empty()) return;
+    std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    long long count = (long long)v.size();
+    uint64_t sum = fnv1a(v.data(), v.size() * sizeof(double));
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&count, sizeof(count), 1, f) == 1 &&
+              std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size() && std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (ok) std::rename(tmp.c_str(), path.c_str());
+    else std::remove(tmp.c_str());
+}
+
 }  // namespace
 
 const double* rys_table_host() {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_host.empty()) g_host = build_table();
+    if (g_host.empty()) {
+        const std::string path = cache_path();
+        if (!load_cache(path, g_host)) {
+            g_host = build_table();
+            store_cache(path, g_host);
+        }
+    }
     return g_host.data();
 }
 
