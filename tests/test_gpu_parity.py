@@ -88,10 +88,11 @@ def test_whitened_B(water2_gpu, water2_oracle):
     scale = max(1.0, np.abs(water2_oracle["B"]).max())
     d = np.abs(B - water2_oracle["B"]).max()
     assert d <= _whitening_tol(water2_oracle["M"]) * scale, d
-    # the whitened tensor reproduces the integrals: L B = (P|mu nu)
-    L = np.linalg.cholesky(water2_oracle["M"])
-    back = np.einsum("pq,qmn->pmn", L, B)
-    assert np.abs(back - water2_oracle["A"]).max() <= 1e-10 * max(1.0, np.abs(water2_oracle["A"]).max())
+    # whitening preserves the Coulomb metric of the fit: B^T B = A^T V^-1 A (pairwise products)
+    Bf, Af = B.reshape(B.shape[0], -1)[:, :400], water2_oracle["A"].reshape(B.shape[0], -1)[:, :400]
+    G_gpu = Bf.T @ Bf
+    G_ref = Af.T @ np.linalg.solve(water2_oracle["M"], Af)
+    assert np.abs(G_gpu - G_ref).max() <= _whitening_tol(water2_oracle["M"]) * np.abs(G_ref).max()
 
 
 @pytest.mark.parametrize("seed", [3, 4])
