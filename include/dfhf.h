@@ -135,6 +135,19 @@ int df_get_matrix(df_handle* h, int which, double* out);
  * by Rys quadrature). A test hook for the device routine the integral kernels use. 1 <= nroots <= 4. */
 int df_rys(const double* T, int count, int nroots, double* x, double* w);
 
+/* Coulomb matrix J (n x n, device pointer) for the density D (n x n, device pointer) without any
+ * device allocation; the paper has no counterpart. For callers that cannot call cudaMalloc (a host
+ * application that owns all device memory through its own allocator, or a latency-critical loop that
+ * cannot afford an allocation's synchronisation or failure). Same kernels and result as the J of
+ * df_jk; the scratch (packed density, gamma, packed J) lives in a 48 MiB array inside the library,
+ * which every GPU that loads the library holds until exit. Requires df_build_B. Systems needing more
+ * than 6,291,456 doubles of scratch (2 packed rows of B + naux; about n <= 2400) are rejected with
+ * DF_E_ARG and a message in df_last_error. Work is enqueued on the handle's stream and the call returns
+ * without waiting. The first call on a device looks up the array's device address (once per device),
+ * so make that first call before any stream capture. All calls share the array: calls that overlap on
+ * the GPU race; calls ordered on one stream are safe. */
+int df_coulomb_noalloc(df_handle* h, const double* D, double* J);
+
 /* Host-side set-up without a GPU: builds and validates the Rys root/weight table (Gauss rules of the
  * Boys-function measure) and caches it as rys_table.bin beside the library (or at $DFHF_TABLE_CACHE).
  * Optional: the first integral call does the same. Returns DF_E_NUMERIC if the table fails its check. */

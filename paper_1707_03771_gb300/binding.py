@@ -16,7 +16,8 @@ DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, 
 DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
-            "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error"]
+            "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
+            "df_coulomb_noalloc"]
 
 
 class Atom(ctypes.Structure):
@@ -72,6 +73,7 @@ def load(path: str | None = None):
     L.df_get_matrix.argtypes = [c_void_p, c_int, dp]
     L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
     L.df_prepare.argtypes = []
+    L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -154,6 +156,10 @@ class Handle:
         """J, K with device pointers (e.g. torch tensors' data_ptr())."""
         rc = load().df_jk(self.h, D_ptr, C_ptr, nocc, J_ptr, K_ptr, 1, precision, slices)
         self._check(rc, "df_jk")
+
+    def coulomb_noalloc(self, D_ptr, J_ptr):
+        """J for device D through df_coulomb_noalloc (no device allocation inside the call)."""
+        self._check(load().df_coulomb_noalloc(self.h, D_ptr, J_ptr), "df_coulomb_noalloc")
 
     def scf(self, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
             incremental=0, screen_tau=0.0):

@@ -218,3 +218,24 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
 }
 
 }  // namespace dfhf
+
+namespace dfhf {
+
+// The Coulomb build with every scratch buffer supplied by the caller and no split of the auxiliary
+// sum: Dw and Jp hold `row` doubles each, gamma `naux`. Each scratch element is written before it
+// is read within the call, so nothing has to start at zero. No allocation, no synchronisation.
+void coulomb_with_scratch(cudaStream_t s, const double* B, const Packing& pk, int naux, int n, const double* dD,
+                          double* dJ, double* Dw, double* gamma, double* Jp) {
+    pack_density_kernel<<<dim3(pk.nt, pk.nt), 256, 0, s>>>(dD, n, Dw);
+    DF_CHECK_LAUNCH();
+    gamma_kernel<<<naux, 256, 0, s>>>(B, pk.row, Dw, gamma);
+    DF_CHECK_LAUNCH();
+    const long long c2 = pk.row / 2;
+    coulomb_kernel<<<dim3((unsigned)((c2 + 255) / 256), 1), 256, 0, s>>>(B, pk.row, naux, gamma, 1, Jp);
+    DF_CHECK_LAUNCH();
+    const long long nn = (long long)n * n;
+    unpack_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Jp, n, dJ);
+    DF_CHECK_LAUNCH();
+}
+
+}  // namespace dfhf
