@@ -177,7 +177,7 @@ void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, dou
     const int ldy = ((nocc + 31) / 32) * 32;
     pad_occupied(h, dC, nocc, ldy);
     if (precision == DF_PREC_SPLIT)
-        exchange_split(h, nocc, slices, dK);
+        exchange_split(h, dC, nocc, slices, dK);
     else
         exchange_fp64(h, nocc, dK);
 }

@@ -170,7 +170,7 @@ int k_splits(const df_handle* h);
 void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* dout);
 
 // split precision (split_k.cu)
-void exchange_split(df_handle* h, int nocc, int slices, double* dK);
+void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK);
 void free_split(df_handle* h);
 
 // SCF (scf.cu)

@@ -1,13 +1,567 @@
-// Split-precision exchange (filled in below the FP64 path).
+// Split-precision exchange: K = sum_P Y_P Y_P^T with Y_P = B_P C_occ (paper eq. 1 first form and
+// eq. 2 first form) on the BF16 tensor cores, with FP64 accuracy recovered by error-free splitting
+// (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 95 (2012)).
+//
+// Splitting. A vector x sharing one power-of-two scale 2^e (max|x| < 2^e) is written exactly as
+//   x = 2^e sum_{s=1..S} m_s 2^{-7 s} + r,   m_1 in [-128, 128], m_s in [-64, 64] (s > 1),
+// with integers m_s (exact in BF16) and |r| <= 2^{e - 7 S - 1}. Scales: per row (P, mu) of B over nu,
+// per column i of C over nu, per (mu, block of auxiliary rows) of Y over (P, i).
+// Products. sum_k m_s(a_k) m_t(b_k) over a chunk of at most 640 terms is an integer below 2^24 even
+// when all pairs with s + t = L are summed into one accumulator, so the FP32 tensor-core sums are
+// exact whatever the hardware's rounding. Pairs with s + t <= S + 1 are kept (the dropped pairs are
+// below 2^{-7(S+1)} relative). After each chunk the integer sums are scaled by the exact power of
+// two 2^{e_a + e_b - 7 L} and added into float-float accumulators (hi, lo) with Knuth's TwoSum.
+// Y leaves its kernel as (hi, lo) pairs, is re-split per (mu, block of P), and K leaves as (hi, lo)
+// partial sums that are combined in FP64.
+// MMA: mma.sync m16n8k16 BF16 -> FP32 (warp-level), operands staged in shared memory by cp.async.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dfhf {
 
-void exchange_split(df_handle* h, int nocc, int slices, double* dK) {
-    (void)h; (void)nocc; (void)slices; (void)dK;
-    throw Error{DF_E_ARG, "split-precision exchange is not available in this build"};
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int KT = 32;             // contraction tile (elements)
+constexpr int LDS = KT + 8;        // padded shared-memory row (bf16): 80 B, conflict-free ldmatrix
+constexpr int CHUNK_TILES = 20;    // 640-element exact chunks
+constexpr int SMAX = 4;
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// x (already scaled so |x| < 1) -> S integer slices
+template <int S>
+__device__ __forceinline__ void split_fp64(double x, bf16* out, long long stride) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const double t = x * 128.0;
+        const double m = rint(t);
+        x = t - m;
+        out[s * stride] = __float2bfloat16_rn((float)m);
+    }
 }
 
-void free_split(df_handle* h) { (void)h; }
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += err;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned* r, const bf16* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsigned* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ------------------------------------------------------------------------------------------------
+// one-time split of B: packed FP64 rows -> Bs[s][P][mu][nu] (np x np per P), exponent per (P, mu)
+// ------------------------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) split_b_kernel(const double* __restrict__ B, long long row, int n, int np,
+                                                      bf16* __restrict__ Bs, long long sstride,
+                                                      int* __restrict__ Be) {
+    const int mu = blockIdx.x;
+    const long long P = blockIdx.y;
+    const double* Bp = B + P * row;
+    double mx = 0.0;
+    if (mu < n)
+        for (int nu = threadIdx.x; nu < n; nu += blockDim.x) mx = fmax(mx, fabs(Bp[packed_index(mu, nu)]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    if (threadIdx.x == 0) Be[P * np + mu] = e;
+    bf16* out = Bs + (P * np + mu) * (long long)np;
+    for (int nu = threadIdx.x; nu < np; nu += blockDim.x) {
+        const double x = (mu < n && nu < n) ? ldexp(Bp[packed_index(mu, nu)], -e) : 0.0;
+        split_fp64<S>(x, out + nu, sstride);
+    }
+}
+
+// C (n x nocc row-major) -> Cs[s][i][nu] (ldy x np), exponent per column i
+template <int S>
+__global__ void __launch_bounds__(256) split_c_kernel(const double* __restrict__ C, int n, int nocc, int np, int ldy,
+                                                      bf16* __restrict__ Cs, long long sstride,
+                                                      int* __restrict__ Ce) {
+    const int i = blockIdx.x;
+    double mx = 0.0;
+    if (i < nocc)
+        for (int nu = threadIdx.x; nu < n; nu += blockDim.x) mx = fmax(mx, fabs(C[(long long)nu * nocc + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    if (threadIdx.x == 0) Ce[i] = e;
+    for (int nu = threadIdx.x; nu < np; nu += blockDim.x) {
+        const double x = (i < nocc && nu < n) ? ldexp(C[(long long)nu * nocc + i], -e) : 0.0;
+        split_fp64<S>(x, Cs + (long long)i * np + nu, sstride);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Shared GEMM core: a CTA of WM x WN warps, warp tile 32 x 32; A rows and B rows (= output columns)
+// both K-contiguous in global memory with leading dimensions lda, ldb. Per k-tile the CTA stages the
+// S slices of A (BM x KT) and of B (BN x KT) and accumulates level accumulators acc[L-2].
+// ------------------------------------------------------------------------------------------------
+template <int S>
+struct Frag {
+    float acc[S][2][4][4];   // [level][m16][n8][4]
+    float hi[2][4][4], lo[2][4][4];
+};
+
+template <int S>
+__device__ __forceinline__ void zero_acc(Frag<S>& f) {
+#pragma unroll
+    for (int L = 0; L < S; ++L)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f.acc[L][a][b][c] = 0.f;
+}
+
+// stage one k-tile of all slices: A rows [0, BM), B rows [0, BN), cp.async 16-byte pieces
+template <int S>
+__device__ __forceinline__ void stage_tile(bf16* sA, bf16* sB, const bf16* A, long long lda, long long astr,
+                                           int a_rows, const bf16* Bm, long long ldb, long long bstr, int b_rows,
+                                           int k0) {
+    const int pieces_a = S * a_rows * (KT / 8);
+    for (int p = threadIdx.x; p < pieces_a; p += blockDim.x) {
+        const int s = p / (a_rows * (KT / 8));
+        const int rem = p % (a_rows * (KT / 8));
+        const int r = rem / (KT / 8), c = (rem % (KT / 8)) * 8;
+        cp_async16(sA + (s * a_rows + r) * LDS + c, A + s * astr + r * lda + k0 + c);
+    }
+    const int pieces_b = S * b_rows * (KT / 8);
+    for (int p = threadIdx.x; p < pieces_b; p += blockDim.x) {
+        const int s = p / (b_rows * (KT / 8));
+        const int rem = p % (b_rows * (KT / 8));
+        const int r = rem / (KT / 8), c = (rem % (KT / 8)) * 8;
+        cp_async16(sB + (s * b_rows + r) * LDS + c, Bm + s * bstr + r * ldb + k0 + c);
+    }
+}
+
+// MMAs of one staged k-tile: warp (wm, wn) covers A rows wm*32.., B rows wn*32..
+template <int S>
+__device__ __forceinline__ void mma_tile(Frag<S>& f, const bf16* sA, int a_rows, const bf16* sB, int b_rows, int wm,
+                                         int wn, int lane) {
+#pragma unroll
+    for (int kk = 0; kk < KT; kk += 16) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            unsigned afr[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const bf16* p = sA + (s * a_rows + wm * 32 + mi * 16 + (lane & 15)) * LDS + kk + (lane >> 4) * 8;
+                ldmatrix_x4(afr[mi], p);
+            }
+#pragma unroll
+            for (int t = 0; t < S - s; ++t) {   // s + t <= S - 1 (0-based) <=> level s + t + 2 <= S + 1
+                unsigned bfr[4][2];
+#pragma unroll
+                for (int j = 0; j < 4; j += 2) {
+                    const int q = lane >> 3, r = lane & 7;
+                    const bf16* p = sB + (t * b_rows + wn * 32 + (j + (q >> 1)) * 8 + r) * LDS + kk + (q & 1) * 8;
+                    unsigned v[4];
+                    ldmatrix_x4(v, p);
+                    bfr[j][0] = v[0];
+                    bfr[j][1] = v[1];
+                    bfr[j + 1][0] = v[2];
+                    bfr[j + 1][1] = v[3];
+                }
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) mma_bf16(f.acc[s + t][mi][j], afr[mi], bfr[j]);
+            }
+        }
+    }
+}
+
+// drain: hi/lo += acc[L] * 2^{ea(row) + eb(col) - 7 (L + 2)}, then acc = 0
+template <int S>
+__device__ __forceinline__ void drain(Frag<S>& f, const int* ea, const int* eb, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int er = ea[mi * 16 + g + 8 * h];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int ec = eb[j * 8 + 2 * t + c];
+                    // levels are combined with exact power-of-two factors; smaller levels are added last
+#pragma unroll
+                    for (int L = S - 1; L >= 0; --L) {
+                        const float x = f.acc[L][mi][j][2 * h + c] * pow2f(er + ec - 7 * (L + 2));
+                        two_sum_acc(f.hi[mi][j][2 * h + c], f.lo[mi][j][2 * h + c], x);
+                        f.acc[L][mi][j][2 * h + c] = 0.f;
+                    }
+                }
+        }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Y = B_P C (split): CTA = P, 64 rows mu, 32*WN columns i; output (hi, lo) pairs Y[P][mu][i]
+// ------------------------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ Bs, long long bstr,
+                                                      const int* __restrict__ Be, const bf16* __restrict__ Cs,
+                                                      long long cstr, const int* __restrict__ Ce, int np, int ldy,
+                                                      float2* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int WN = blockDim.x / 64;
+    const int BN = 32 * WN;
+    bf16* sA = reinterpret_cast<bf16*>(smem_raw);                 // [2][S][64][LDS]
+    bf16* sB = sA + 2 * S * 64 * LDS;                               // [2][S][BN][LDS]
+    int* sEa = reinterpret_cast<int*>(sB + 2 * S * BN * LDS);       // [64]
+    int* sEb = sEa + 64;                                            // [BN]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int m0 = blockIdx.x * 64;
+    const int n0 = blockIdx.z * BN;
+    const long long P = blockIdx.y;
+    const bf16* A = Bs + (P * np + m0) * (long long)np;
+    const bf16* Bm = Cs + (long long)n0 * np;
+    for (int r = threadIdx.x; r < 64; r += blockDim.x) sEa[r] = Be[P * np + m0 + r];
+    for (int c = threadIdx.x; c < BN; c += blockDim.x) sEb[c] = (n0 + c < ldy) ? Ce[n0 + c] : 0;
+    const int b_rows = min(BN, ldy - n0);
+    Frag<S> f;
+    zero_acc(f);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f.hi[a][b][c] = f.lo[a][b][c] = 0.f;
+    const int nk = np / KT;
+    stage_tile<S>(sA, sB, A, np, bstr, 64, Bm, np, cstr, b_rows, 0);
+    cp_async_commit();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk)
+            stage_tile<S>(sA + (cur ^ 1) * S * 64 * LDS, sB + (cur ^ 1) * S * BN * LDS, A, np, bstr, 64, Bm, np, cstr,
+                          b_rows, (kt + 1) * KT);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        if (wn * 32 < b_rows) mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * BN * LDS, BN, wm, wn, lane);
+        __syncthreads();
+        if ((kt + 1) % CHUNK_TILES == 0 || kt + 1 == nk) drain<S>(f, sEa + wm * 32, sEb + wn * 32, lane);
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int mu = m0 + wm * 32 + mi * 16 + g + 8 * h;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = n0 + wn * 32 + j * 8 + 2 * t + c;
+                    if (i < ldy) Y[(P * np + mu) * (long long)ldy + i] = make_float2(f.hi[mi][j][2 * h + c], f.lo[mi][j][2 * h + c]);
+                }
+        }
+}
+
+// Y (hi, lo) -> Ys[s][P][mu][i] with one exponent per (mu, block of PB auxiliary rows); warp per (mu, block)
+template <int S>
+__global__ void __launch_bounds__(256) split_y_kernel(const float2* __restrict__ Y, int naux, int np, int ldy, int PB,
+                                                      bf16* __restrict__ Ys, long long sstride, int* __restrict__ Ye) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nblk = (naux + PB - 1) / PB;
+    if (warp >= nblk * np) return;
+    const int mu = warp % np, b = warp / np;
+    const int p0 = b * PB, p1 = min(naux, p0 + PB);
+    float mx = 0.f;
+    for (int P = p0; P < p1; ++P)
+        for (int i = lane; i < ldy; i += 32) mx = fmaxf(mx, fabsf(Y[((long long)P * np + mu) * ldy + i].x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) {
+        frexpf(mx, &e);
+        e += 1;   // hi + lo may round up past the next power of two: keep |y| 2^-e < 1
+    }
+    if (lane == 0) Ye[(long long)b * np + mu] = e;
+    const float sc = pow2f(-e);
+    for (int P = p0; P < p1; ++P)
+        for (int i = lane; i < ldy; i += 32) {
+            const long long idx = ((long long)P * np + mu) * ldy + i;
+            const float2 y = Y[idx];
+            float r = y.x * sc;
+            float rl = y.y * sc;
+            bf16* out = Ys + idx;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const float tt = r * 128.f;
+                const float m = rintf(tt);
+                r = (tt - m) + rl * 128.f;
+                rl = 0.f;
+                out[s * sstride] = __float2bfloat16_rn(m);
+            }
+        }
+}
+
+// ------------------------------------------------------------------------------------------------
+// K partial sums over a range of auxiliary blocks for lower tile pair (I >= J) of 64 x 64
+// ------------------------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(128) k_split_kernel(const bf16* __restrict__ Ys, long long sstride,
+                                                      const int* __restrict__ Ye, int naux, int np, int ldy, int PB,
+                                                      int nsplit, const int2* __restrict__ tiles,
+                                                      float2* __restrict__ Kpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16* sA = reinterpret_cast<bf16*>(smem_raw);     // [2][S][64][LDS]
+    bf16* sB = sA + 2 * S * 64 * LDS;                 // [2][S][64][LDS]
+    __shared__ int sEa[64], sEb[64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int2 IJ = tiles[blockIdx.x];
+    const int nblk = (naux + PB - 1) / PB;
+    const int b0 = (int)((long long)nblk * blockIdx.y / nsplit), b1 = (int)((long long)nblk * (blockIdx.y + 1) / nsplit);
+    Frag<S> f;
+    zero_acc(f);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f.hi[a][b][c] = f.lo[a][b][c] = 0.f;
+    const int kt_per_P = ldy / KT;
+    for (int blk = b0; blk < b1; ++blk) {
+        const int p0 = blk * PB, p1 = min(naux, p0 + PB);
+        __syncthreads();
+        for (int r = threadIdx.x; r < 64; r += blockDim.x) {
+            sEa[r] = Ye[(long long)blk * np + IJ.x * 64 + r];
+            sEb[r] = Ye[(long long)blk * np + IJ.y * 64 + r];
+        }
+        const int nk = (p1 - p0) * kt_per_P;
+        auto src = [&](int kt, int rowtile) {
+            const int P = p0 + kt / kt_per_P;
+            return Ys + ((long long)P * np + rowtile * 64) * ldy + (kt % kt_per_P) * KT;
+        };
+        stage_tile<S>(sA, sB, src(0, IJ.x), ldy, sstride, 64, src(0, IJ.y), ldy, sstride, 64, 0);
+        cp_async_commit();
+        for (int kt = 0; kt < nk; ++kt) {
+            const int cur = kt & 1;
+            if (kt + 1 < nk)
+                stage_tile<S>(sA + (cur ^ 1) * S * 64 * LDS, sB + (cur ^ 1) * S * 64 * LDS, src(kt + 1, IJ.x), ldy,
+                              sstride, 64, src(kt + 1, IJ.y), ldy, sstride, 64, 0);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * 64 * LDS, 64, wm, wn, lane);
+            __syncthreads();
+        }
+        drain<S>(f, sEa + wm * 32, sEb + wn * 32, lane);
+    }
+    float2* Kp = Kpart + (long long)blockIdx.y * np * np;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int mu = IJ.x * 64 + wm * 32 + mi * 16 + g + 8 * h;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int nu = IJ.y * 64 + wn * 32 + j * 8 + 2 * t + c;
+                    Kp[(long long)mu * np + nu] = make_float2(f.hi[mi][j][2 * h + c], f.lo[mi][j][2 * h + c]);
+                }
+        }
+}
+
+__global__ void k_split_reduce_kernel(const float2* __restrict__ Kpart, int nsplit, int np, int n, double* __restrict__ K) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int a = (int)(idx / n), b = (int)(idx % n);
+    if (a / 64 < b / 64) { const int t = a; a = b; b = t; }
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) {
+        const float2 v = Kpart[(long long)q * np * np + (long long)a * np + b];
+        s += (double)v.x + (double)v.y;
+    }
+    K[idx] = s;
+}
+
+inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct SplitState {
+    int S = 0;
+    int np = 0;
+    bf16* Bs = nullptr;
+    int* Be = nullptr;
+    bf16* Cs = nullptr;
+    int* Ce = nullptr;
+    float2* Y = nullptr;
+    bf16* Ys = nullptr;
+    int* Ye = nullptr;
+    float2* Kpart = nullptr;
+    int ldy = 0;
+    int nsplit = 0;
+    int PB = 0;
+};
+
+void free_split(df_handle* h) {
+    SplitState* st = h->split;
+    if (!st) return;
+    cudaFree(st->Bs);
+    cudaFree(st->Be);
+    cudaFree(st->Cs);
+    cudaFree(st->Ce);
+    cudaFree(st->Y);
+    cudaFree(st->Ys);
+    cudaFree(st->Ye);
+    cudaFree(st->Kpart);
+    delete st;
+    h->split = nullptr;
+}
+
+namespace {
+
+template <int S>
+void prepare_b(df_handle* h, SplitState* st) {
+    const long long np = st->np;
+    const long long bstr = (long long)h->naux * np * np;
+    DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * S * bstr));
+    DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * h->naux * np));
+    split_b_kernel<S><<<dim3((unsigned)np, h->naux), 256, 0, h->stream>>>(h->B.p, h->pk.row, h->n, (int)np, st->Bs, bstr,
+                                                                        st->Be);
+    DF_CHECK_LAUNCH();
+}
+
+template <int S>
+void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK) {
+    cudaStream_t s = h->stream;
+    const int np = st->np, ldy = st->ldy, naux = h->naux;
+    const long long cstr = (long long)ldy * np;
+    split_c_kernel<S><<<ldy, 256, 0, s>>>(dC, h->n, nocc, np, ldy, st->Cs, cstr, st->Ce);
+    DF_CHECK_LAUNCH();
+    // Y = B C: CTA tiles of 64 rows x 32*WN columns
+    int WN = std::min(5, ldy / 32);
+    const int BN = 32 * WN;
+    const size_t smem = (size_t)2 * S * (64 + BN) * LDS * sizeof(bf16) + (64 + BN) * sizeof(int);
+    DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 gy(np / 64, naux, (ldy + BN - 1) / BN);
+    y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np, ldy,
+                                                 st->Y);
+    DF_CHECK_LAUNCH();
+    const long long nblk = (naux + st->PB - 1) / st->PB;
+    const long long ystr = (long long)naux * np * ldy;
+    split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
+    DF_CHECK_LAUNCH();
+    const int nt = np / 64;
+    const int ntiles = nt * (nt + 1) / 2;
+    const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
+    DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
+    k_split_kernel<S><<<dim3(ntiles, st->nsplit), 128, ksmem, s>>>(st->Ys, ystr, st->Ye, naux, np, ldy, st->PB,
+                                                                    st->nsplit, h->ktiles.p, st->Kpart);
+    DF_CHECK_LAUNCH();
+    const long long nn = (long long)h->n * h->n;
+    k_split_reduce_kernel<<<nblocks(nn, 256), 256, 0, s>>>(st->Kpart, st->nsplit, np, h->n, dK);
+    DF_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// K from the split path for the occupied coefficients dC (n x nocc, device)
+void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK) {
+    if (slices < 2 || slices > SMAX) throw Error{DF_E_ARG, "slices must be 2..4"};
+    if (h->pk.np % 64) throw Error{DF_E_ARG, "internal: padded size not a multiple of 64"};
+    SplitState* st = h->split;
+    if (st && st->S != slices) {
+        free_split(h);
+        st = nullptr;
+    }
+    cudaEvent_t e0, e1;
+    DF_CUDA(cudaEventCreate(&e0));
+    DF_CUDA(cudaEventCreate(&e1));
+    DF_CUDA(cudaEventRecord(e0, h->stream));
+    if (!st) {
+        st = new SplitState();
+        h->split = st;
+        st->S = slices;
+        st->np = h->pk.np;
+        switch (slices) {
+            case 2: prepare_b<2>(h, st); break;
+            case 3: prepare_b<3>(h, st); break;
+            default: prepare_b<4>(h, st); break;
+        }
+    }
+    const int ldy = ((nocc + 31) / 32) * 32;
+    if (ldy != st->ldy) {
+        cudaFree(st->Cs);
+        cudaFree(st->Ce);
+        cudaFree(st->Y);
+        cudaFree(st->Ys);
+        cudaFree(st->Ye);
+        cudaFree(st->Kpart);
+        st->ldy = ldy;
+        st->PB = std::max(1, (CHUNK_TILES * KT) / ldy);
+        if (ldy > CHUNK_TILES * KT) throw Error{DF_E_ARG, "split exchange supports nocc <= 640"};
+        const int nt = st->np / 64;
+        const int ntiles = nt * (nt + 1) / 2;
+        st->nsplit = std::max(1, std::min((8 * 152 + ntiles - 1) / ntiles, (h->naux + st->PB - 1) / st->PB));
+        const long long np = st->np;
+        DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * slices * (long long)ldy * np));
+        DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
+        DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
+        DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * slices * (long long)h->naux * np * ldy));
+        const long long nblk = (h->naux + st->PB - 1) / st->PB;
+        DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * nblk * np));
+        DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
+    }
+    switch (slices) {
+        case 2: run_split<2>(h, st, dC, nocc, dK); break;
+        case 3: run_split<3>(h, st, dC, nocc, dK); break;
+        default: run_split<4>(h, st, dC, nocc, dK); break;
+    }
+    DF_CUDA(cudaEventRecord(e1, h->stream));
+    DF_CUDA(cudaEventSynchronize(e1));
+    h->timings_ms[8] = elapsed_ms(e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
 
 }  // namespace dfhf
