@@ -4,11 +4,14 @@ Workload: a seeded 32-water cluster (1600 basis functions, 4384 auxiliary functi
 orbitals, packed whitened B of 46.7 GB resident in HBM), synthetic geometry and even-tempered bases.
 
 A step is one density-fitted Fock build from the resident B: gamma = B.D, J = B^T gamma, the
-half-transform Y = B C_occ and K = sum_P Y_P Y_P^T (paper eqs. 1-3). `value` is seconds per J/K
-build with inputs already on the device (CUDA events on the library's stream, max over ranks);
-`e2e` is the same through the C ABI with host buffers (D and C_occ copied in, J and K copied out
-inside the timed region). `time_to_converge_s` is one full SCF (integrals + whitening + iterations)
-from the core-Hamiltonian guess to |dE| < 1e-10 Eh.
+half-transform Y = B C_occ and K = sum_P Y_P Y_P^T (paper eqs. 1-3). By default the exchange is the
+split-precision form (BF16 Ozaki slices on the tensor cores) at the 5 slices the SCF uses for its
+final iterations; --precision fp64 times the FP64 form. `value` is seconds per J/K build with inputs
+already on the device (CUDA events on the stream the library launches on, max over ranks); `e2e` is
+the same through the C ABI with host buffers (D and C_occ copied in, J and K copied out inside the
+timed region). `time_to_converge_s` is one full SCF (integrals + whitening + iterations) from the
+core-Hamiltonian guess to |dE| < 1e-10 Eh and max|FDS - SDF| < 1e-7; `compare` holds the per-iteration
+time of the early-iteration split form (3 slices) and of the FP64 form on the same density.
 
 Inputs (46.7 GB of B) are far larger than L2 (126 MB), so no flush is needed between steps.
 Under torchrun with N > 1 each rank runs an independent replica (the path has no exchange step).
@@ -111,13 +114,14 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     if ws > 1:
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0 or ws > 1:
-        build.build()
+    build.build()
     if ws > 1:
         tdist.barrier()
     lib = binding.load()
     system = clusters.workload(args.workload)
-    precision = binding.DF_PREC_SPLIT if args.precision == "split" else binding.DF_PREC_FP64
+    split = args.precision == "split"
+    prec = binding.DF_PREC_SPLIT if split else binding.DF_PREC_FP64
+    S = args.slices
 
     t0 = time.perf_counter()
     h = binding.Handle(system)
@@ -128,10 +132,10 @@ def gpu_arm(args):
 
     # a physical density for the timed builds: the core-Hamiltonian orbitals
     n, nocc = h.n, h.nocc
-    S, H = h.matrix("S"), h.matrix("H")
-    s, U = np.linalg.eigh(S)
-    X = U[:, s > 1e-7] / np.sqrt(s[s > 1e-7])
-    e, Cp = np.linalg.eigh(X.T @ H @ X)
+    S_ov, H = h.matrix("S"), h.matrix("H")
+    sv, U = np.linalg.eigh(S_ov)
+    X = U[:, sv > 1e-7] / np.sqrt(sv[sv > 1e-7])
+    _, Cp = np.linalg.eigh(X.T @ H @ X)
     C = np.ascontiguousarray((X @ Cp)[:, :nocc])
     D = 2 * C @ C.T
     dev = torch.device("cuda", local)
@@ -140,78 +144,102 @@ def gpu_arm(args):
     dJ = torch.empty((n, n), dtype=torch.float64, device=dev)
     dK = torch.empty((n, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
     lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
 
-    def step():
-        h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, args.slices)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        tdist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    dom_ms = []
-    with ClockSampler(local) as clocks:
+    def run_steps(precision, slices, warmup, steps):
+        for _ in range(warmup):
+            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
         torch.cuda.synchronize()
+        if ws > 1:
+            tdist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per = []
         ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-            dom_ms.append(dict(h.timings()))
+        for _ in range(steps):
+            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
+            per.append(dict(h.timings()))
         ev1.record(stream)
         torch.cuda.synchronize()
-    total_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
+        total = ev0.elapsed_time(ev1)
+        if ws > 1:
+            t = torch.tensor([total], dtype=torch.float64, device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            total = float(t.item())
+        return total / steps, per
 
-    # end to end through the C ABI with host buffers
-    Jh = np.empty((n, n))
-    Kh = np.empty((n, n))
+    with ClockSampler(local) as clocks:
+        ms_per_step, per = run_steps(prec, S, args.warmup, args.steps)
+
+    # end to end through the C ABI with host buffers (copies in and out inside the timed region)
     lib.df_set_stream(h.h, None)
     for _ in range(2):
-        h.jk(D, C, precision, args.slices)
+        Jh, Kh = h.jk(D, C, prec, S)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        Jh, Kh = h.jk(D, C, precision, args.slices)
+        Jh, Kh = h.jk(D, C, prec, S)
     e2e_s = (time.perf_counter() - t1) / args.steps
     if ws > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
 
-    # time to a converged SCF (B already built: add the build time measured above)
-    ttc = None
-    scf_info = None
+    # comparisons: the other precisions on the same density
+    compare = {}
+    if split:
+        compare["split_s3_s_per_iter"] = run_steps(binding.DF_PREC_SPLIT, 3, 1, 3)[0] / 1000.0
+        if not args.no_fp64_compare:
+            compare["fp64_s_per_iter"] = run_steps(binding.DF_PREC_FP64, 0, 1, 2)[0] / 1000.0
+    lib.df_set_stream(h.h, None)
+
+    # time to a converged SCF from the core-Hamiltonian guess (B already built: its build time is added)
+    ttc = {}
+    scf_info = {}
     if args.ttc:
-        res = h.scf(precision=precision, slices=args.slices)
-        ttc = t_build + res["t_total_s"]
-        scf_info = {"energy": res["energy"], "iterations": res["iterations"], "converged": bool(res["converged"]),
-                    "t_iter_s": res["t_iter_s"], "t_jk_s": res["t_jk_s"]}
+        runs = [("split" if split else "fp64", prec)]
+        if split and args.compare_ttc:
+            runs.append(("fp64", binding.DF_PREC_FP64))
+        for label, p in runs:
+            res = h.scf(precision=p, slices=3)
+            ttc[label] = t_build + res["t_total_s"]
+            scf_info[label] = {"energy": res["energy"], "iterations": res["iterations"],
+                               "converged": bool(res["converged"]), "t_iter_s": res["t_iter_s"],
+                               "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"]}
 
-    # roofline of the dominant kernel
     peaks, peak_src = _peaks()
-    keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms"]
-    avg = {k: float(np.mean([d[k] for d in dom_ms])) for k in keys}
-    naux, npair = h.naux, n * (n + 1) // 2
-    if precision == binding.DF_PREC_FP64:
-        dom = "ytransform_ms"
-        flops = 2.0 * naux * n * n * nocc          # Y = B C: 2 naux n^2 nocc
-        achieved = flops / (avg[dom] * 1e-3) / 1e12
+    keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
+            "split_other_ms"]
+    avg = {k: float(np.mean([d[k] for d in per])) for k in keys}
+    naux = h.naux
+    alg_k_flops = 2.0 * naux * n * n * nocc + 1.0 * naux * n * n * nocc   # Y = B C and K = sum Y Y^T
+    if not split:
+        flops = 2.0 * naux * n * n * nocc
+        achieved = flops / (avg["ytransform_ms"] * 1e-3) / 1e12
         roofline = {"kernel": "y_transform_kernel (FP64 DFMA)", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "measured FP64 DFMA loop (not in MEASURED_PEAKS.json)", "traffic": None}
+                    "peak_source": "measured FP64 DFMA loop over 152 SMs (not in MEASURED_PEAKS.json)",
+                    "traffic": None}
     else:
-        dom = "kcontract_ms"
-        hw_flops = float(os.environ.get("DF_SPLIT_HW_FLOPS", "0"))
-        achieved = hw_flops / (avg[dom] * 1e-3) / 1e12 if hw_flops else None
+        npad = (n + 63) // 64 * 64
+        ldy = (nocc + 31) // 32 * 32
+        pairs = S * (S + 1) // 2
+        nt = npad // 64
+        y_hw = pairs * 2.0 * naux * npad * npad * ldy
+        k_hw = pairs * 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * naux * ldy
+        y_tf = y_hw / (avg["split_y_ms"] * 1e-3) / 1e12
+        k_tf = k_hw / (avg["split_k_ms"] * 1e-3) / 1e12
+        dom_y = avg["split_y_ms"] >= avg["split_k_ms"]
+        achieved = y_tf if dom_y else k_tf
         pk = peaks.get("bf16_tflops")
-        roofline = {"kernel": "split K contraction (BF16 tensor cores)", "bound": "tensor", "achieved": achieved,
-                    "peak": pk, "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None,
-                    "peak_source": peak_src, "traffic": None}
+        roofline = {"kernel": ("y_split_kernel" if dom_y else "k_split_kernel") + " (BF16 mma.sync, Ozaki slices)",
+                    "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / pk if pk else None,
+                    "peak_source": f"{peak_src} bf16_tflops (cuBLAS burst)",
+                    "traffic": None,
+                    "y_split_tflops": y_tf, "k_split_tflops": k_tf,
+                    "fp64_equivalent_tflops": alg_k_flops / ((avg["split_y_ms"] + avg["split_k_ms"] + avg["split_other_ms"]) * 1e-3) / 1e12}
     kernel_ms = {k: round(v, 3) for k, v in avg.items()}
 
     cpu = None
@@ -222,21 +250,23 @@ def gpu_arm(args):
         "metric": METRIC, "value": ms_per_step / 1000.0, "unit": "s/iter (DF J+K build)",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == binding.DF_PREC_FP64 else f"bf16x{args.slices}-split/f32acc/f64",
+        "dtype": f"bf16 Ozaki x{S} slices, exact f32 chunk sums, f32x2 accumulate, f64 J" if split else "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: seeded water cluster, n={n}, naux={naux}, nocc={nocc}, "
                                f"packed B {h.naux * h.packed_row * 8 / 1e9:.1f} GB",
-                   "precision": args.precision, "l2": "inputs larger than L2 (B resident, no flush)",
+                   "precision": args.precision + (f" (S={S})" if split else ""),
+                   "l2": "inputs larger than L2 (B resident, no flush)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": e2e_s, "unit": "s/iter (DF J+K build, host buffers)",
                 "h2d_bytes_per_step": int(D.nbytes + C.nbytes), "d2h_bytes_per_step": int(Jh.nbytes + Kh.nbytes)},
-        "gpu_launches": args.steps * launches_per_step(precision),
+        "gpu_launches": args.steps * launches_per_step(prec),
         "roofline": roofline,
         "kernel_ms": kernel_ms,
+        "compare": compare,
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
                     "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
-        "time_to_converge_s": ttc, "scf": scf_info,
+        "time_to_converge_s": ttc or None, "scf": scf_info or None,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
@@ -253,8 +283,9 @@ def ctypes_ptr(v):
 
 
 def launches_per_step(precision):
-    # pack D, gamma, coulomb, split-sum, unpack J, pad C, Y transform, K contraction, K reduce
-    return 9 if precision == 0 else 9 + 2
+    # J: pack D, gamma, coulomb, split-sum, unpack; pad C; then FP64 K: Y transform, K contraction, K reduce,
+    # or split K: split C, split Y-GEMM, re-split Y, split K contraction, reduce
+    return 9 if precision == 0 else 11
 
 
 def _oracle_jk_sample(system, rows, rng):
@@ -323,8 +354,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default=os.environ.get("DF_BENCH_PRECISION", "fp64"), choices=["fp64", "split"])
-    ap.add_argument("--slices", type=int, default=3)
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--slices", type=int, default=5, help="slices of the timed split builds (the late-SCF precision)")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--compare-ttc", action="store_true", help="also time a full FP64 SCF (minutes)")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

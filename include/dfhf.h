@@ -54,7 +54,7 @@ typedef struct { int atom; int l; double exponent; double center[3]; } df_shell;
 
 /* Precision of the K contraction (paper silent; the split form is this library's design). */
 #define DF_PREC_FP64 0       /* every step in FP64 */
-#define DF_PREC_SPLIT 1      /* K from split BF16 slices on tensor cores, FP32 accumulate, FP64 sum */
+#define DF_PREC_SPLIT 1      /* K from split BF16 slices on tensor cores, exact FP32 chunk sums, float-float sum */
 
 #define DF_GUESS_CORE 0      /* core-Hamiltonian guess */
 
@@ -65,7 +65,9 @@ typedef struct {
     int diis_size;           /* Pulay subspace (<= 16) */
     int guess;               /* DF_GUESS_* */
     int precision;           /* DF_PREC_* */
-    int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..4) */
+    int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..5) in early iterations;
+                                once max|e| < 1e-4 the exchange is built with 5 slices, and the SCF
+                                converges only on those builds */
     int incremental;         /* 1: late iterations build K from the density change (split mode) */
     double screen_tau;       /* drop shell triples whose bound is below tau (0 = none) */
 } df_options;
@@ -82,6 +84,7 @@ typedef struct {
     int converged;
     int status;              /* DF_OK or DF_E_NOTCONV / DF_E_NUMERIC */
     int n_dropped;           /* orbitals removed by canonical orthogonalisation */
+    int ramp_iteration;      /* split mode: first iteration built with 5 slices (0 if never) */
     double t_build_s;        /* df_build_B time within this call (0 if B was already built) */
     double t_iter_s;         /* total SCF iteration time */
     double t_jk_s;           /* time in J/K builds */
@@ -115,7 +118,7 @@ int df_build_B(df_handle* h, double screen_tau, int keep_3c);
  * 0: host pointers, copied in and out inside the call. precision: DF_PREC_FP64 or DF_PREC_SPLIT
  * (slices as in df_options). Requires df_build_B. */
 int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* J, double* K,
-          int device_ptrs, int precision, int slices);
+          int device_ptrs, int precision, int slices);   /* slices: 2..5 for DF_PREC_SPLIT */
 
 /* Full SCF from the core-Hamiltonian guess; builds B first if needed (screen_tau from opts).
  * Results in *out; returns out->status. */
@@ -158,7 +161,8 @@ int df_set_stream(df_handle* h, void* stream);
 
 /* Per-phase device times of the last df_build_B / df_jk in milliseconds (CUDA events):
  * [0] 1e+metric, [1] three-centre ERI, [2] Cholesky+inverse, [3] whitening, [4] gamma, [5] J,
- * [6] Y half-transform, [7] K contraction, [8] split slicing. Up to `count` values are written. */
+ * [6] Y half-transform (FP64), [7] K contraction (FP64), [8] whole split exchange, [9] split Y,
+ * [10] split K contraction, [11] split slicing and reduction. Up to `count` (<= 16) values are written. */
 int df_timings(const df_handle* h, double* ms, int count);
 
 void df_free(df_handle* h);

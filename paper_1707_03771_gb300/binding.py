@@ -39,7 +39,8 @@ class Result(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("e_nuc", ctypes.c_double), ("e_one", ctypes.c_double),
                 ("e_coul", ctypes.c_double), ("e_exch", ctypes.c_double), ("last_dE", ctypes.c_double),
                 ("last_err", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
-                ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("t_build_s", ctypes.c_double),
+                ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("ramp_iteration", ctypes.c_int),
+                ("t_build_s", ctypes.c_double),
                 ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double)]
 
     def as_dict(self):
@@ -190,7 +191,7 @@ class Handle:
         out = np.zeros(16)
         load().df_timings(self.h, _dp(out), 16)
         keys = ["init_ms", "eri3c_ms", "cholesky_ms", "whiten_ms", "gamma_ms", "coulomb_ms", "ytransform_ms",
-                "kcontract_ms", "split_ms"]
+                "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms", "split_other_ms"]
         return dict(zip(keys, out[:len(keys)]))
 
     def close(self):

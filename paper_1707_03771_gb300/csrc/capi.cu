@@ -329,7 +329,7 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
           int precision, int slices) {
     if (!h || !D || !C_occ || !J || !K || nocc < 1 || nocc > h->n) return DF_E_ARG;
     if (precision != DF_PREC_FP64 && precision != DF_PREC_SPLIT) return DF_E_ARG;
-    if (precision == DF_PREC_SPLIT && (slices < 2 || slices > 4)) return DF_E_ARG;
+    if (precision == DF_PREC_SPLIT && (slices < 2 || slices > 5)) return DF_E_ARG;
     if (!h->built) return fail(h, Error{DF_E_STATE, "df_jk before df_build_B"});
     try {
         DF_CUDA(cudaSetDevice(h->device));
@@ -362,7 +362,7 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
-    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 4)) return DF_E_ARG;
+    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     try {
         DF_CUDA(cudaSetDevice(h->device));
         return scf_drive(h, opts, out);

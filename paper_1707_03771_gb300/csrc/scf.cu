@@ -22,6 +22,8 @@ void build_B(df_handle* h, double tau, bool keep);
 namespace {
 
 constexpr int DIIS_MAX = 16;
+constexpr int SPLIT_LATE_SLICES = 5;      // slices of the late split-precision exchange builds
+constexpr double SPLIT_RAMP_ERR = 1e-4;   // max|e| below which the late builds start
 
 __global__ void build_x_kernel(const double* __restrict__ U, const double* __restrict__ s, int n, int first, int nX,
                                double* __restrict__ X) {
@@ -276,9 +278,10 @@ int scf_drive(df_handle* h, const df_options* o, df_result* r) {
         DF_CUDA(cudaEventCreate(&ej1));
         const auto t_iter = clk::now();
         int it = 0;
+        int slices = o->slices;   // split mode: o->slices early, SPLIT_LATE_SLICES once max|e| < SPLIT_RAMP_ERR
         for (it = 1; it <= o->max_iter; ++it) {
             DF_CUDA(cudaEventRecord(ej0, s));
-            jk_dispatch(h, h->Dm.p, h->dC.p, nocc, h->dJ.p, h->dK.p, o->precision, o->slices);
+            jk_dispatch(h, h->Dm.p, h->dC.p, nocc, h->dJ.p, h->dK.p, o->precision, slices);
             DF_CUDA(cudaEventRecord(ej1, s));
             fock_kernel<<<nblk(nn), 256, 0, s>>>(h->H.p, h->dJ.p, h->dK.p, nn, h->F.p);
             DF_CHECK_LAUNCH();
@@ -319,9 +322,14 @@ int scf_drive(df_handle* h, const df_options* o, df_result* r) {
             r->last_err = err;
             r->last_dE = (it > 1) ? energy - e_old : 0.0;
             r->iterations = it;
-            if (it > 1 && std::fabs(energy - e_old) < o->conv_E && err < o->conv_err) {
+            const bool late_ready = o->precision != DF_PREC_SPLIT || slices >= SPLIT_LATE_SLICES;
+            if (it > 1 && late_ready && std::fabs(energy - e_old) < o->conv_E && err < o->conv_err) {
                 status = DF_OK;
                 break;
+            }
+            if (o->precision == DF_PREC_SPLIT && slices < SPLIT_LATE_SLICES && err < SPLIT_RAMP_ERR) {
+                slices = SPLIT_LATE_SLICES;
+                r->ramp_iteration = it + 1;
             }
             e_old = energy;
             // DIIS bookkeeping: store F, dots, solve, combine

@@ -6,9 +6,9 @@
 //   x = 2^e sum_{s=1..S} m_s 2^{-7 s} + r,   m_1 in [-128, 128], m_s in [-64, 64] (s > 1),
 // with integers m_s (exact in BF16) and |r| <= 2^{e - 7 S - 1}. Scales: per row (P, mu) of B over nu,
 // per column i of C over nu, per (mu, block of auxiliary rows) of Y over (P, i).
-// Products. sum_k m_s(a_k) m_t(b_k) over a chunk of at most 640 terms is an integer below 2^24 even
-// when all pairs with s + t = L are summed into one accumulator, so the FP32 tensor-core sums are
-// exact whatever the hardware's rounding. Pairs with s + t <= S + 1 are kept (the dropped pairs are
+// Products. sum_k m_s(a_k) m_t(b_k) over a chunk of at most 512 terms is an integer below 2^24 even
+// when all pairs with s + t = L are summed into one accumulator (at most 2^14 + 3 * 2^13 per term for
+// S <= 5), so the FP32 tensor-core sums are exact whatever the hardware's rounding. Pairs with s + t <= S + 1 are kept (the dropped pairs are
 // below 2^{-7(S+1)} relative). After each chunk the integer sums are scaled by the exact power of
 // two 2^{e_a + e_b - 7 L} and added into float-float accumulators (hi, lo) with Knuth's TwoSum.
 // Y leaves its kernel as (hi, lo) pairs, is re-split per (mu, block of P), and K leaves as (hi, lo)
@@ -28,10 +28,11 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int KT = 32;             // contraction tile (elements)
 constexpr int LDS = KT + 8;        // padded shared-memory row (bf16): 80 B, conflict-free ldmatrix
-constexpr int CHUNK_TILES = 20;    // 640-element exact chunks
-constexpr int SMAX = 4;
+constexpr int CHUNK_TILES = 16;    // 512-element exact chunks
+constexpr int SMAX = 5;
 
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// exact 2^e as a float; 0 below the normal range (such contributions are below 2^-126 of the scale)
+__device__ __forceinline__ float pow2f(int e) { return e < -126 ? 0.f : __int_as_float((127 + min(e, 127)) << 23); }
 
 // x (already scaled so |x| < 1) -> S integer slices
 template <int S>
@@ -136,10 +137,12 @@ __global__ void __launch_bounds__(256) split_c_kernel(const double* __restrict__
 // both K-contiguous in global memory with leading dimensions lda, ldb. Per k-tile the CTA stages the
 // S slices of A (BM x KT) and of B (BN x KT) and accumulates level accumulators acc[L-2].
 // ------------------------------------------------------------------------------------------------
+// warp tile 32 x (8 NJ): NJ = 4 for S <= 3, 2 for S >= 4 (keeps the S level accumulators in registers)
 template <int S>
 struct Frag {
-    float acc[S][2][4][4];   // [level][m16][n8][4]
-    float hi[2][4][4], lo[2][4][4];
+    static constexpr int NJ = S <= 3 ? 4 : 2;
+    float acc[S][2][NJ][4];   // [level][m16][n8][4]
+    float hi[2][NJ][4], lo[2][NJ][4];
 };
 
 template <int S>
@@ -149,9 +152,19 @@ __device__ __forceinline__ void zero_acc(Frag<S>& f) {
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
+            for (int b = 0; b < Frag<S>::NJ; ++b)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) f.acc[L][a][b][c] = 0.f;
+}
+
+template <int S>
+__device__ __forceinline__ void zero_hilo(Frag<S>& f) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < Frag<S>::NJ; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f.hi[a][b][c] = f.lo[a][b][c] = 0.f;
 }
 
 // stage one k-tile of all slices: A rows [0, BM), B rows [0, BN), cp.async 16-byte pieces
@@ -175,7 +188,7 @@ __device__ __forceinline__ void stage_tile(bf16* sA, bf16* sB, const bf16* A, lo
     }
 }
 
-// MMAs of one staged k-tile: warp (wm, wn) covers A rows wm*32.., B rows wn*32..
+// MMAs of one staged k-tile: warp (wm, wn) covers A rows wm*32.., B rows wn*WNT..
 template <int S>
 __device__ __forceinline__ void mma_tile(Frag<S>& f, const bf16* sA, int a_rows, const bf16* sB, int b_rows, int wm,
                                          int wn, int lane) {
@@ -191,11 +204,12 @@ __device__ __forceinline__ void mma_tile(Frag<S>& f, const bf16* sA, int a_rows,
             }
 #pragma unroll
             for (int t = 0; t < S - s; ++t) {   // s + t <= S - 1 (0-based) <=> level s + t + 2 <= S + 1
-                unsigned bfr[4][2];
+                constexpr int NJ = Frag<S>::NJ;
+                unsigned bfr[NJ][2];
 #pragma unroll
-                for (int j = 0; j < 4; j += 2) {
+                for (int j = 0; j < NJ; j += 2) {
                     const int q = lane >> 3, r = lane & 7;
-                    const bf16* p = sB + (t * b_rows + wn * 32 + (j + (q >> 1)) * 8 + r) * LDS + kk + (q & 1) * 8;
+                    const bf16* p = sB + (t * b_rows + wn * NJ * 8 + (j + (q >> 1)) * 8 + r) * LDS + kk + (q & 1) * 8;
                     unsigned v[4];
                     ldmatrix_x4(v, p);
                     bfr[j][0] = v[0];
@@ -206,7 +220,7 @@ __device__ __forceinline__ void mma_tile(Frag<S>& f, const bf16* sA, int a_rows,
 #pragma unroll
                 for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) mma_bf16(f.acc[s + t][mi][j], afr[mi], bfr[j]);
+                    for (int j = 0; j < NJ; ++j) mma_bf16(f.acc[s + t][mi][j], afr[mi], bfr[j]);
             }
         }
     }
@@ -222,7 +236,7 @@ __device__ __forceinline__ void drain(Frag<S>& f, const int* ea, const int* eb, 
         for (int h = 0; h < 2; ++h) {
             const int er = ea[mi * 16 + g + 8 * h];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < Frag<S>::NJ; ++j)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const int ec = eb[j * 8 + 2 * t + c];
@@ -246,8 +260,9 @@ __global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ B
                                                       long long cstr, const int* __restrict__ Ce, int np, int ldy,
                                                       float2* __restrict__ Y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WNT = 8 * Frag<S>::NJ;
     const int WN = blockDim.x / 64;
-    const int BN = 32 * WN;
+    const int BN = WNT * WN;
     bf16* sA = reinterpret_cast<bf16*>(smem_raw);                 // [2][S][64][LDS]
     bf16* sB = sA + 2 * S * 64 * LDS;                               // [2][S][BN][LDS]
     int* sEa = reinterpret_cast<int*>(sB + 2 * S * BN * LDS);       // [64]
@@ -264,12 +279,7 @@ __global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ B
     const int b_rows = min(BN, ldy - n0);
     Frag<S> f;
     zero_acc(f);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) f.hi[a][b][c] = f.lo[a][b][c] = 0.f;
+    zero_hilo(f);
     const int nk = np / KT;
     stage_tile<S>(sA, sB, A, np, bstr, 64, Bm, np, cstr, b_rows, 0);
     cp_async_commit();
@@ -281,9 +291,9 @@ __global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ B
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        if (wn * 32 < b_rows) mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * BN * LDS, BN, wm, wn, lane);
+        if (wn * WNT < b_rows) mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * BN * LDS, BN, wm, wn, lane);
         __syncthreads();
-        if ((kt + 1) % CHUNK_TILES == 0 || kt + 1 == nk) drain<S>(f, sEa + wm * 32, sEb + wn * 32, lane);
+        if ((kt + 1) % CHUNK_TILES == 0 || kt + 1 == nk) drain<S>(f, sEa + wm * 32, sEb + wn * WNT, lane);
     }
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -292,10 +302,10 @@ __global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ B
         for (int h = 0; h < 2; ++h) {
             const int mu = m0 + wm * 32 + mi * 16 + g + 8 * h;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < Frag<S>::NJ; ++j)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const int i = n0 + wn * 32 + j * 8 + 2 * t + c;
+                    const int i = n0 + wn * WNT + j * 8 + 2 * t + c;
                     if (i < ldy) Y[(P * np + mu) * (long long)ldy + i] = make_float2(f.hi[mi][j][2 * h + c], f.lo[mi][j][2 * h + c]);
                 }
         }
@@ -316,10 +326,7 @@ __global__ void __launch_bounds__(256) split_y_kernel(const float2* __restrict__
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
-    if (mx > 0.f) {
-        frexpf(mx, &e);
-        e += 1;   // hi + lo may round up past the next power of two: keep |y| 2^-e < 1
-    }
+    if (mx > 0.f) frexpf(mx, &e);   // |hi + lo| 2^-e <= 1 + 2^-24, so |m_1| <= 128 still holds
     if (lane == 0) Ye[(long long)b * np + mu] = e;
     const float sc = pow2f(-e);
     for (int P = p0; P < p1; ++P)
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(256) split_y_kernel(const float2* __restrict__
 // K partial sums over a range of auxiliary blocks for lower tile pair (I >= J) of 64 x 64
 // ------------------------------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(128) k_split_kernel(const bf16* __restrict__ Ys, long long sstride,
+__global__ void __launch_bounds__(256) k_split_kernel(const bf16* __restrict__ Ys, long long sstride,
                                                       const int* __restrict__ Ye, int naux, int np, int ldy, int PB,
                                                       int nsplit, const int2* __restrict__ tiles,
                                                       float2* __restrict__ Kpart) {
@@ -357,14 +364,10 @@ __global__ void __launch_bounds__(128) k_split_kernel(const bf16* __restrict__ Y
     const int2 IJ = tiles[blockIdx.x];
     const int nblk = (naux + PB - 1) / PB;
     const int b0 = (int)((long long)nblk * blockIdx.y / nsplit), b1 = (int)((long long)nblk * (blockIdx.y + 1) / nsplit);
+    constexpr int WNT = 8 * Frag<S>::NJ;
     Frag<S> f;
     zero_acc(f);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) f.hi[a][b][c] = f.lo[a][b][c] = 0.f;
+    zero_hilo(f);
     const int kt_per_P = ldy / KT;
     for (int blk = b0; blk < b1; ++blk) {
         const int p0 = blk * PB, p1 = min(naux, p0 + PB);
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(128) k_split_kernel(const bf16* __restrict__ Y
             mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * 64 * LDS, 64, wm, wn, lane);
             __syncthreads();
         }
-        drain<S>(f, sEa + wm * 32, sEb + wn * 32, lane);
+        drain<S>(f, sEa + wm * 32, sEb + wn * WNT, lane);
     }
     float2* Kp = Kpart + (long long)blockIdx.y * np * np;
     const int g = lane >> 2, t = lane & 3;
@@ -401,10 +404,10 @@ __global__ void __launch_bounds__(128) k_split_kernel(const bf16* __restrict__ Y
         for (int h = 0; h < 2; ++h) {
             const int mu = IJ.x * 64 + wm * 32 + mi * 16 + g + 8 * h;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < Frag<S>::NJ; ++j)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const int nu = IJ.y * 64 + wn * 32 + j * 8 + 2 * t + c;
+                    const int nu = IJ.y * 64 + wn * WNT + j * 8 + 2 * t + c;
                     Kp[(long long)mu * np + nu] = make_float2(f.hi[mi][j][2 * h + c], f.lo[mi][j][2 * h + c]);
                 }
         }
@@ -472,21 +475,24 @@ void prepare_b(df_handle* h, SplitState* st) {
 }
 
 template <int S>
-void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK) {
+void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK, cudaEvent_t* ev) {
     cudaStream_t s = h->stream;
     const int np = st->np, ldy = st->ldy, naux = h->naux;
     const long long cstr = (long long)ldy * np;
     split_c_kernel<S><<<ldy, 256, 0, s>>>(dC, h->n, nocc, np, ldy, st->Cs, cstr, st->Ce);
     DF_CHECK_LAUNCH();
     // Y = B C: CTA tiles of 64 rows x 32*WN columns
-    int WN = std::min(5, ldy / 32);
-    const int BN = 32 * WN;
+    constexpr int WNT = 8 * Frag<S>::NJ;
+    const int WN = std::min(5, ldy / WNT);
+    const int BN = WNT * WN;
     const size_t smem = (size_t)2 * S * (64 + BN) * LDS * sizeof(bf16) + (64 + BN) * sizeof(int);
     DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 gy(np / 64, naux, (ldy + BN - 1) / BN);
+    DF_CUDA(cudaEventRecord(ev[0], s));
     y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np, ldy,
                                                  st->Y);
     DF_CHECK_LAUNCH();
+    DF_CUDA(cudaEventRecord(ev[1], s));
     const long long nblk = (naux + st->PB - 1) / st->PB;
     const long long ystr = (long long)naux * np * ldy;
     split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
@@ -495,9 +501,11 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const int ntiles = nt * (nt + 1) / 2;
     const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
     DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
-    k_split_kernel<S><<<dim3(ntiles, st->nsplit), 128, ksmem, s>>>(st->Ys, ystr, st->Ye, naux, np, ldy, st->PB,
+    DF_CUDA(cudaEventRecord(ev[2], s));
+    k_split_kernel<S><<<dim3(ntiles, st->nsplit), 2 * (64 / WNT) * 32, ksmem, s>>>(st->Ys, ystr, st->Ye, naux, np, ldy, st->PB,
                                                                     st->nsplit, h->ktiles.p, st->Kpart);
     DF_CHECK_LAUNCH();
+    DF_CUDA(cudaEventRecord(ev[3], s));
     const long long nn = (long long)h->n * h->n;
     k_split_reduce_kernel<<<nblocks(nn, 256), 256, 0, s>>>(st->Kpart, st->nsplit, np, h->n, dK);
     DF_CHECK_LAUNCH();
@@ -505,31 +513,41 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
 
 }  // namespace
 
-// K from the split path for the occupied coefficients dC (n x nocc, device)
+// K from the split path for the occupied coefficients dC (n x nocc, device).
+// B is split once; when HBM allows, with SMAX slices, so that builds with fewer slices (early SCF
+// iterations) and with SMAX slices (late iterations) share one split: the first S slices of an
+// SMAX-slice split are exactly the S-slice split (same exponents, same rounding sequence).
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK) {
-    if (slices < 2 || slices > SMAX) throw Error{DF_E_ARG, "slices must be 2..4"};
+    if (slices < 2 || slices > SMAX) throw Error{DF_E_ARG, "slices must be 2..5"};
     if (h->pk.np % 64) throw Error{DF_E_ARG, "internal: padded size not a multiple of 64"};
     SplitState* st = h->split;
-    if (st && st->S != slices) {
+    if (st && st->S < slices) {
         free_split(h);
         st = nullptr;
     }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, ev[4];
     DF_CUDA(cudaEventCreate(&e0));
     DF_CUDA(cudaEventCreate(&e1));
+    for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
     DF_CUDA(cudaEventRecord(e0, h->stream));
+    const int ldy = ((nocc + 31) / 32) * 32;
     if (!st) {
         st = new SplitState();
         h->split = st;
-        st->S = slices;
         st->np = h->pk.np;
-        switch (slices) {
+        const long long np = st->np;
+        size_t free_b = 0, total_b = 0;
+        DF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const double per_slice = 2.0 * h->naux * np * np + 2.0 * h->naux * np * ldy;
+        const double fixed = 8.0 * h->naux * np * ldy + 16.0 * np * np + (4ull << 30);
+        st->S = (free_b > SMAX * per_slice + fixed) ? SMAX : slices;
+        switch (st->S) {
             case 2: prepare_b<2>(h, st); break;
             case 3: prepare_b<3>(h, st); break;
-            default: prepare_b<4>(h, st); break;
+            case 4: prepare_b<4>(h, st); break;
+            default: prepare_b<5>(h, st); break;
         }
     }
-    const int ldy = ((nocc + 31) / 32) * 32;
     if (ldy != st->ldy) {
         cudaFree(st->Cs);
         cudaFree(st->Ce);
@@ -539,29 +557,34 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         cudaFree(st->Kpart);
         st->ldy = ldy;
         st->PB = std::max(1, (CHUNK_TILES * KT) / ldy);
-        if (ldy > CHUNK_TILES * KT) throw Error{DF_E_ARG, "split exchange supports nocc <= 640"};
+        if (ldy > CHUNK_TILES * KT) throw Error{DF_E_ARG, "split exchange supports nocc <= 512"};
         const int nt = st->np / 64;
         const int ntiles = nt * (nt + 1) / 2;
         st->nsplit = std::max(1, std::min((8 * 152 + ntiles - 1) / ntiles, (h->naux + st->PB - 1) / st->PB));
         const long long np = st->np;
-        DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * slices * (long long)ldy * np));
+        DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * st->S * (long long)ldy * np));
         DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
         DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
-        DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * slices * (long long)h->naux * np * ldy));
+        DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * (long long)h->naux * np * ldy));
         const long long nblk = (h->naux + st->PB - 1) / st->PB;
         DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * nblk * np));
         DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
     }
     switch (slices) {
-        case 2: run_split<2>(h, st, dC, nocc, dK); break;
-        case 3: run_split<3>(h, st, dC, nocc, dK); break;
-        default: run_split<4>(h, st, dC, nocc, dK); break;
+        case 2: run_split<2>(h, st, dC, nocc, dK, ev); break;
+        case 3: run_split<3>(h, st, dC, nocc, dK, ev); break;
+        case 4: run_split<4>(h, st, dC, nocc, dK, ev); break;
+        default: run_split<5>(h, st, dC, nocc, dK, ev); break;
     }
     DF_CUDA(cudaEventRecord(e1, h->stream));
     DF_CUDA(cudaEventSynchronize(e1));
     h->timings_ms[8] = elapsed_ms(e0, e1);
+    h->timings_ms[9] = elapsed_ms(ev[0], ev[1]);    // Y = B C (split)
+    h->timings_ms[10] = elapsed_ms(ev[2], ev[3]);   // K contraction (split)
+    h->timings_ms[11] = h->timings_ms[8] - h->timings_ms[9] - h->timings_ms[10];   // slicing, reduce
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    for (auto& e : ev) cudaEventDestroy(e);
 }
 
 }  // namespace dfhf

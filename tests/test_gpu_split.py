@@ -16,7 +16,7 @@ def lib():
 
 
 @pytest.mark.parametrize("name", ["water2", "water8"])
-@pytest.mark.parametrize("slices", [2, 3, 4])
+@pytest.mark.parametrize("slices", [2, 3, 4, 5])
 def test_split_k_against_fp64(lib, name, slices):
     system = clusters.workload(name)
     rng = np.random.default_rng(5)
@@ -30,7 +30,10 @@ def test_split_k_against_fp64(lib, name, slices):
     rel = np.abs(Ks - K64).max() / np.abs(K64).max()
     e_rel = abs(np.sum(D * (Ks - K64))) / abs(np.sum(D * K64))
     print(f"{name} S={slices}: max rel dK {rel:.3e}, rel d tr(DK) {e_rel:.3e}")
-    bound = {2: 2e-3, 3: 2e-5, 4: 2e-7}[slices]
+    # 7 bits per slice below each row's power-of-two scale; an exact CPU emulation of the same splitting
+    # shows the dynamic range inside a scaled row and the cancellation in K cost up to ~2^5 of that:
+    # bound 2^(7 - 7 S) relative to max |K|
+    bound = 2.0 ** (7 - 7 * slices)
     assert rel <= bound, rel
     assert np.abs(Ks - Ks.T).max() <= 1e-14 * np.abs(Ks).max() + 0.0
 
@@ -40,6 +43,7 @@ def test_split_scf_energy(lib):
     with lib.Handle(system) as h:
         e64 = h.scf()["energy"]
         res = h.scf(precision=lib.DF_PREC_SPLIT, slices=3)
-    print(f"water8: E64 {e64:.10f}  Esplit {res['energy']:.10f}  dE {res['energy'] - e64:.3e}")
+    print(f"water8: E64 {e64:.10f}  Esplit {res['energy']:.10f}  dE {res['energy'] - e64:.3e} "
+          f"iterations {res['iterations']} ramp at {res['ramp_iteration']}")
     assert res["converged"]
     assert abs(res["energy"] - e64) <= 1e-6
