@@ -12,6 +12,8 @@ namespace dfhf {
 
 void rys_eval(const double* dT, int count, int n, double* dx, double* dw, cudaStream_t s);
 const double* rys_table_host();
+void whiten_float_float(cudaStream_t s, int m, long long ncol, const double* Linv, double* Lff, double* A, double* B,
+                        long long ld, bool restore_a);
 
 namespace {
 
@@ -159,7 +161,13 @@ void build_B(df_handle* h, double tau, bool keep) {
     DF_CHECK_LAUNCH();
     DF_CUDA(cudaEventRecord(ev[2], s));
     h->B.alloc(rows);
-    dtrmm_lower(s, na, h->pk.row, h->Linv.p, h->A3c.p, h->B.p, h->pk.row);
+    {
+        DevBuf<double> lff;
+        lff.alloc((size_t)na * na);
+        whiten_float_float(s, na, h->pk.row, h->Linv.p, lff.p, h->A3c.p, h->B.p, h->pk.row, keep);
+        DF_CUDA(cudaStreamSynchronize(s));
+        lff.release();
+    }
     DF_CUDA(cudaEventRecord(ev[3], s));
     DF_CUDA(cudaEventSynchronize(ev[3]));
     h->timings_ms[1] = elapsed_ms(ev[0], ev[1]);

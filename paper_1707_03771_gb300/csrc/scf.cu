@@ -327,12 +327,19 @@ int scf_drive(df_handle* h, const df_options* o, df_result* r) {
                 status = DF_OK;
                 break;
             }
+            bool ramp = false;
             if (o->precision == DF_PREC_SPLIT && slices < SPLIT_LATE_SLICES && err < SPLIT_RAMP_ERR) {
                 slices = SPLIT_LATE_SLICES;
                 r->ramp_iteration = it + 1;
+                ramp = true;
             }
             e_old = energy;
-            // DIIS bookkeeping: store F, dots, solve, combine
+            // DIIS bookkeeping: store F, dots, solve, combine. At the precision ramp the subspace is
+            // restarted from the current Fock matrix: the earlier ones carry the coarser exchange.
+            if (ramp) {
+                for (int q : order) present[q] = 0;
+                order.clear();
+            }
             DF_CUDA(cudaMemcpyAsync(h->diisF.p + (long long)slot * nn, h->F.p, nn * sizeof(double),
                                     cudaMemcpyDeviceToDevice, s));
             present[slot] = 1;
