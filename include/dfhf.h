@@ -124,6 +124,18 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
  * Results in *out; returns out->status. */
 int scf_run(df_handle* h, const df_options* opts, df_result* out);
 
+/* Batched SCF: nmol independent molecules (distinct handles on one device) solved together. Every
+ * iteration enqueues all unfinished molecules' work on their own streams before waiting on any, so
+ * kernels of different molecules overlap on the GPU; each molecule needs one host synchronisation per
+ * iteration (its energy and error). B is built first for handles that lack it. out[i] receives
+ * molecule i's result; the return value is DF_OK if all converged, else the first failing status. */
+int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out);
+
+/* Per-iteration record of the last scf_run: up to max_rows rows of 6 doubles
+ * (iteration, energy, energy change, max|X^T(FDS - SDF)X|, exchange slices (0 = FP64), J/K build ms).
+ * Returns the number of rows the run produced (which may exceed max_rows), or a negative DF_E_*. */
+int df_scf_history(const df_handle* h, double* out, int max_rows);
+
 /* Copy rows [p0, p0+count) of an auxiliary-indexed tensor, unpacked to (count, n, n):
  * which = 0: unwhitened (P|mu nu) (needs keep_3c), 1: whitened B. Host output. */
 int df_get_rows(df_handle* h, int which, int p0, int count, double* out);

@@ -17,7 +17,7 @@ DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
-            "df_coulomb_noalloc"]
+            "df_coulomb_noalloc", "df_scf_history", "scf_run_batch"]
 
 
 class Atom(ctypes.Structure):
@@ -75,6 +75,8 @@ def load(path: str | None = None):
     L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
     L.df_prepare.argtypes = []
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.df_scf_history.argtypes = [c_void_p, dp, c_int]
+    L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -171,6 +173,16 @@ class Handle:
             self._check(rc, "scf_run")
         return r.as_dict()
 
+    def history(self):
+        """Per-iteration rows of the last SCF: iteration, energy, dE, max|e|, slices, J/K ms."""
+        L = load()
+        n = L.df_scf_history(self.h, None, 0)
+        if n < 0:
+            raise DFError(n, "df_scf_history")
+        out = np.zeros((max(n, 1), 6))
+        L.df_scf_history(self.h, _dp(out), n)
+        return out[:n]
+
     def rows(self, which, p0, count):
         out = np.empty((count, self.n, self.n))
         self._check(load().df_get_rows(self.h, which, p0, count, _dp(out)), "df_get_rows")
@@ -210,6 +222,58 @@ class Handle:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
+              screen_tau=0.0):
+    """Solve several molecules together (scf_run_batch); returns one result dict per handle."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[hd.h.value for hd in handles])
+    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, 0, screen_tau)
+    out = (Result * n)()
+    rc = load().scf_run_batch(hs, n, ctypes.byref(o), out)
+    if rc not in (DF_OK, DF_E_NOTCONV):
+        raise DFError(rc, "scf_run_batch: " + load().df_last_error(handles[0].h).decode())
+    return [out[i].as_dict() for i in range(n)]
+
+
+def estimate_bytes(system, precision=DF_PREC_FP64, slices=5) -> int:
+    """Device memory one molecule needs for its B tensors (and split slices), for wave planning."""
+    n, naux, nocc = system.nbf, system.naux, system.nocc
+    nt = (n + 63) // 64
+    npad = nt * 64
+    row = nt * (nt + 1) // 2 * 64 * 64
+    total = 2 * naux * row * 8 + 40 * n * n * 8
+    if precision == DF_PREC_SPLIT:
+        ldy = (nocc + 31) // 32 * 32
+        total += slices * naux * npad * npad * 2 + naux * npad * ldy * (8 + 2 * slices)
+    return int(total)
+
+
+def scf_waves(systems, budget_bytes, precision=DF_PREC_FP64, slices=3, **kw):
+    """Solve many molecules in waves whose estimated device memory fits `budget_bytes`; each wave is
+    one scf_run_batch. Returns one result dict per system, in order."""
+    results = [None] * len(systems)
+    order = list(range(len(systems)))
+    i = 0
+    while i < len(order):
+        wave, used = [], 0
+        while i < len(order):
+            need = estimate_bytes(systems[order[i]], precision, 5)
+            if wave and used + need > budget_bytes:
+                break
+            wave.append(order[i])
+            used += need
+            i += 1
+        handles = [Handle(systems[k]) for k in wave]
+        try:
+            res = scf_batch(handles, precision=precision, slices=slices, **kw)
+        finally:
+            for h in handles:
+                h.close()
+        for k, r in zip(wave, res):
+            results[k] = r
+    return results
 
 
 def rys(T, nroots):

@@ -380,6 +380,31 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out) {
     }
 }
 
+int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out) {
+    if (!hs || nmol < 1 || !opts || !out) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
+    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
+    int dev = -1;
+    for (int i = 0; i < nmol; ++i) {
+        if (!hs[i]) return DF_E_ARG;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return DF_E_ARG;   // each molecule needs its own handle
+        if (dev < 0) dev = hs[i]->device;
+        if (hs[i]->device != dev) return DF_E_ARG;
+    }
+    try {
+        DF_CUDA(cudaSetDevice(dev));
+        return scf_drive_batch(hs, nmol, opts, out);
+    } catch (const Error& e) {
+        for (int i = 0; i < nmol; ++i) {
+            hs[i]->last_error = e.msg;
+            if (out[i].status == 0 && !out[i].converged) out[i].status = e.code;
+        }
+        return e.code;
+    }
+}
+
 int df_get_rows(df_handle* h, int which, int p0, int count, double* out) {
     if (!h || !out || p0 < 0 || count < 1 || p0 + count > h->naux || (which != 0 && which != 1)) return DF_E_ARG;
     const double* src = which == 0 ? h->A3c.p : h->B.p;
@@ -453,6 +478,14 @@ int df_rys(const double* T, int count, int nroots, double* x, double* w) {
         return e.code;
     }
     return DF_OK;
+}
+
+int df_scf_history(const df_handle* h, double* out, int max_rows) {
+    if (!h || (!out && max_rows > 0) || max_rows < 0) return DF_E_ARG;
+    const int rows = (int)(h->history.size() / 6);
+    const int n = rows < max_rows ? rows : max_rows;
+    for (int i = 0; i < 6 * n; ++i) out[i] = h->history[i];
+    return rows;
 }
 
 int df_prepare(void) {

@@ -143,6 +143,8 @@ struct df_handle {
     int ndrop = 0;
 
     double timings_ms[16] = {0};
+    std::vector<double> history;   // per SCF iteration: iteration, energy, dE, max|e|, slices, J/K ms
+    bool sync_timing = true;       // per-kernel event timings (the batch driver turns them off)
 };
 
 namespace dfhf {
@@ -175,6 +177,7 @@ void free_split(df_handle* h);
 
 // SCF (scf.cu)
 int scf_drive(df_handle* h, const df_options* o, df_result* r);
+int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
 }  // namespace dfhf

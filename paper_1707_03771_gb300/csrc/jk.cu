@@ -159,9 +159,11 @@ void coulomb_fp64(df_handle* h, const double* dD, double* dJ) {
     const long long nn = (long long)h->n * h->n;
     unpack_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(h->Jp.p, h->n, dJ);
     DF_CHECK_LAUNCH();
-    DF_CUDA(cudaEventSynchronize(e2));
-    h->timings_ms[4] = elapsed_ms(e0, e1);
-    h->timings_ms[5] = elapsed_ms(e1, e2);
+    if (h->sync_timing) {
+        DF_CUDA(cudaEventSynchronize(e2));
+        h->timings_ms[4] = elapsed_ms(e0, e1);
+        h->timings_ms[5] = elapsed_ms(e1, e2);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
@@ -187,9 +189,11 @@ void exchange_fp64(df_handle* h, int nocc, double* dK) {
     const int ntiles = pk.nt * (pk.nt + 1) / 2;
     k_syrk_fp64(s, h->Y.p, h->naux, pk.np, ldy, nocc, k_splits(h), h->ktiles.p, ntiles, h->Kpart.p, h->n, dK);
     DF_CUDA(cudaEventRecord(e2, s));
-    DF_CUDA(cudaEventSynchronize(e2));
-    h->timings_ms[6] = elapsed_ms(e0, e1);
-    h->timings_ms[7] = elapsed_ms(e1, e2);
+    if (h->sync_timing) {
+        DF_CUDA(cudaEventSynchronize(e2));
+        h->timings_ms[6] = elapsed_ms(e0, e1);
+        h->timings_ms[7] = elapsed_ms(e1, e2);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
@@ -115,8 +116,9 @@ __global__ void diis_dots_kernel(const double* __restrict__ E, long long len, in
 }
 
 // Solve the Lagrange system [B -1; -1 0][c; l] = [0; -1] over the listed slots by Gaussian
-// elimination with partial pivoting (single thread; m <= 16). coef[slot] receives c; status 0 ok,
-// 1 singular (relative pivot below 1e-14).
+// elimination with partial pivoting (single thread; m <= 16). coef[slot] receives c; status 0 ok.
+// If a relative pivot falls below 1e-14 the system is singular: status 1 and coef selects the newest
+// vector alone (plain F this iteration); the host then drops the oldest vector from the subspace.
 __global__ void diis_solve_kernel(const double* __restrict__ Bm, const int* __restrict__ slots, int m,
                                   double* __restrict__ coef, int* __restrict__ status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -138,6 +140,7 @@ __global__ void diis_solve_kernel(const double* __restrict__ Bm, const int* __re
         for (int r = col + 1; r < N; ++r)
             if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
         if (fabs(A[piv][col]) < 1e-14) {
+            for (int i = 0; i < m; ++i) coef[slots[i]] = (i == m - 1) ? 1.0 : 0.0;
             *status = 1;
             return;
         }
@@ -169,221 +172,315 @@ __global__ void diis_combine_kernel(const double* __restrict__ Fs, long long len
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-struct Solver {
-    df_handle* h;
-    int n, nX;
-    double* work = nullptr;
-    int lwork = 0;
-    int* info = nullptr;
+// One molecule's SCF as a sequence of asynchronous iterations with a single host synchronisation each
+// (the energy terms, max|e| and status words), so that many molecules can advance in lock-step on their
+// own streams (scf_run_batch) while the GPU overlaps their kernels.
+class ScfRun {
+  public:
+    ScfRun(df_handle* h, const df_options* o, df_result* r) : h_(h), o_(*o), r_(r) {}
+    ~ScfRun() { release(); }
+
+    // orthogonaliser and core-Hamiltonian guess (synchronises: the dropped-eigenvalue count is needed)
+    void begin() {
+        t_start_ = clk::now();
+        *r_ = df_result{};
+        r_->e_nuc = h_->e_nuc;
+        if (!h_->built) {
+            const auto t0 = clk::now();
+            build_B(h_, o_.screen_tau, false);
+            r_->t_build_s = std::chrono::duration<double>(clk::now() - t0).count();
+        }
+        n_ = h_->n;
+        nocc_ = h_->nocc;
+        nn_ = (long long)n_ * n_;
+        s_ = h_->stream;
+        dsize_ = std::max(2, std::min(o_.diis_size, DIIS_MAX));
+        slices_ = o_.slices;
+        DF_CUDA(cudaMalloc((void**)&info_, sizeof(int)));
+        DF_CUDA(cudaHostAlloc((void**)&pin_, sizeof(double) * 8, cudaHostAllocDefault));
+        DF_CUDA(cudaHostAlloc((void**)&pin_ctl_, sizeof(int) * (2 * DIIS_MAX + 2), cudaHostAllocDefault));
+        DF_CUDA(cudaEventCreate(&ev_done_));
+        DF_CUDA(cudaEventCreate(&ej0_));
+        DF_CUDA(cudaEventCreate(&ej1_));
+        h_->work1.alloc(nn_);
+        h_->work2.alloc(nn_);
+        h_->work3.alloc(nn_);
+        h_->eps.alloc(n_);
+        DF_CUDA(cudaMemcpyAsync(h_->work1.p, h_->S.p, nn_ * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+        eig(h_->work1.p, n_, h_->eps.p);
+        std::vector<double> sv(n_);
+        DF_CUDA(cudaMemcpyAsync(sv.data(), h_->eps.p, n_ * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        int hinfo = 0;
+        DF_CUDA(cudaMemcpyAsync(&hinfo, info_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaStreamSynchronize(s_));
+        if (hinfo != 0) throw Error{DF_E_NUMERIC, "dsyevd of S failed, info " + std::to_string(hinfo)};
+        int first = 0;
+        while (first < n_ && sv[first] <= 1e-7) ++first;
+        nX_ = n_ - first;
+        if (nX_ < nocc_) throw Error{DF_E_NUMERIC, "orthogonal basis smaller than the occupied space"};
+        h_->nX = nX_;
+        h_->ndrop = first;
+        r_->n_dropped = first;
+        h_->X.alloc((size_t)n_ * nX_);
+        build_x_kernel<<<nblk((long long)n_ * nX_), 256, 0, s_>>>(h_->work1.p, h_->eps.p, n_, first, nX_, h_->X.p);
+        DF_CHECK_LAUNCH();
+        h_->F.alloc(nn_);
+        h_->Fx.alloc(nn_);
+        h_->Dm.alloc(nn_);
+        h_->C.alloc((size_t)n_ * nX_);
+        DF_CUDA(cudaMemsetAsync(h_->C.p, 0, sizeof(double) * n_ * nX_, s_));
+        DF_CUDA(cudaMemsetAsync(h_->eps.p, 0, sizeof(double) * n_, s_));
+        ensure_jk_buffers(h_, nocc_);
+        h_->diisF.alloc((size_t)DIIS_MAX * nn_);
+        h_->diisE.alloc((size_t)DIIS_MAX * nX_ * nX_);
+        h_->diisB.alloc(DIIS_MAX * DIIS_MAX + 8 + DIIS_MAX);   // B matrix | scalars (8) | coef
+        d_B_ = h_->diisB.p;
+        d_scal_ = d_B_ + DIIS_MAX * DIIS_MAX;
+        d_coef_ = d_scal_ + 8;
+        DF_CUDA(cudaMalloc((void**)&d_ints_, sizeof(int) * (2 * DIIS_MAX + 2)));   // present | slots | status
+        DF_CUDA(cudaMemsetAsync(d_ints_, 0, sizeof(int) * (2 * DIIS_MAX + 2), s_));
+        DF_CUDA(cudaMalloc((void**)&Fp_, sizeof(double) * nX_ * nX_));
+        DF_CUDA(cudaMalloc((void**)&T1_, sizeof(double) * n_ * nX_));
+        present_.assign(DIIS_MAX, 0);
+        order_.clear();
+        h_->history.clear();
+        roothaan(h_->H.p);   // core-Hamiltonian guess
+        t_iter_ = clk::now();
+        it_ = 0;
+        done_ = false;
+    }
+
+    bool done() const { return done_; }
+
+    // J/K, Fock, energy, error vector; scalars and status words copied to pinned memory; one event
+    void enqueue_iteration() {
+        ++it_;
+        DF_CUDA(cudaEventRecord(ej0_, s_));
+        jk_dispatch(h_, h_->Dm.p, h_->dC.p, nocc_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+        DF_CUDA(cudaEventRecord(ej1_, s_));
+        fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, h_->F.p);
+        DF_CHECK_LAUNCH();
+        energy_kernel<<<1, 1024, 0, s_>>>(h_->Dm.p, h_->H.p, h_->dJ.p, h_->dK.p, nn_, d_scal_);
+        DF_CHECK_LAUNCH();
+        // error vector e = X^T (FDS - SDF) X, written into the next DIIS slot
+        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->F.p, n_, h_->Dm.p, n_, 0.0, h_->work1.p, n_);
+        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
+        antisym_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->work2.p, n_, h_->work3.p);
+        DF_CHECK_LAUNCH();
+        dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work3.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        slot_ = 0;
+        if ((int)order_.size() < dsize_) {
+            while (present_[slot_]) ++slot_;
+        } else {
+            slot_ = order_.front();
+            order_.erase(order_.begin());
+            present_[slot_] = 0;
+        }
+        double* Eslot = h_->diisE.p + (long long)slot_ * nX_ * nX_;
+        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Eslot, nX_);
+        absmax_kernel<<<1, 1024, 0, s_>>>(Eslot, (long long)nX_ * nX_, d_scal_ + 3);
+        DF_CHECK_LAUNCH();
+        DF_CUDA(cudaMemcpyAsync(pin_, d_scal_, 4 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaMemcpyAsync(pin_ctl_ + 2 * DIIS_MAX, d_ints_ + 2 * DIIS_MAX, sizeof(int), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaMemcpyAsync(pin_ctl_ + 2 * DIIS_MAX + 1, info_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaEventRecord(ev_done_, s_));
+    }
+
+    // wait for the iteration, test convergence; if not done, enqueue DIIS and the Roothaan step
+    void finish_iteration() {
+        DF_CUDA(cudaEventSynchronize(ev_done_));
+        const double this_jk = elapsed_ms(ej0_, ej1_);
+        jk_ms_ += this_jk;
+        if (pin_ctl_[2 * DIIS_MAX + 1] != 0)
+            throw Error{DF_E_NUMERIC, "dsyevd failed, info " + std::to_string(pin_ctl_[2 * DIIS_MAX + 1])};
+        if (pin_ctl_[2 * DIIS_MAX] != 0 && !order_.empty()) {   // last DIIS system was singular
+            const int old = order_.front();
+            if (old != slot_) {
+                present_[old] = 0;
+                order_.erase(order_.begin());
+            }
+        }
+        const double energy = pin_[0] + 0.5 * pin_[1] - 0.5 * pin_[2] + h_->e_nuc;
+        const double err = pin_[3];
+        h_->history.insert(h_->history.end(), {(double)it_, energy, it_ > 1 ? energy - e_old_ : 0.0, err,
+                                               o_.precision == DF_PREC_SPLIT ? (double)slices_ : 0.0, this_jk});
+        if (!std::isfinite(energy) || !std::isfinite(err)) {
+            status_ = DF_E_NUMERIC;
+            return finish();
+        }
+        r_->energy = energy;
+        r_->e_one = pin_[0];
+        r_->e_coul = 0.5 * pin_[1];
+        r_->e_exch = -0.5 * pin_[2];
+        r_->last_err = err;
+        r_->last_dE = (it_ > 1) ? energy - e_old_ : 0.0;
+        r_->iterations = it_;
+        const bool late_ready = o_.precision != DF_PREC_SPLIT || slices_ >= SPLIT_LATE_SLICES;
+        if (it_ > 1 && late_ready && std::fabs(energy - e_old_) < o_.conv_E && err < o_.conv_err) {
+            status_ = DF_OK;
+            return finish();
+        }
+        if (it_ >= o_.max_iter) {
+            status_ = DF_E_NOTCONV;
+            return finish();
+        }
+        e_old_ = energy;
+        bool ramp = false;
+        if (o_.precision == DF_PREC_SPLIT && slices_ < SPLIT_LATE_SLICES && err < SPLIT_RAMP_ERR) {
+            slices_ = SPLIT_LATE_SLICES;
+            r_->ramp_iteration = it_ + 1;
+            ramp = true;
+        }
+        // DIIS: at the precision ramp the subspace restarts from the current Fock matrix (the earlier
+        // ones carry the coarser exchange)
+        if (ramp) {
+            for (int q : order_) present_[q] = 0;
+            order_.clear();
+        }
+        DF_CUDA(cudaMemcpyAsync(h_->diisF.p + (long long)slot_ * nn_, h_->F.p, nn_ * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s_));
+        present_[slot_] = 1;
+        order_.push_back(slot_);
+        for (int q = 0; q < DIIS_MAX; ++q) pin_ctl_[q] = present_[q];
+        for (size_t q = 0; q < order_.size(); ++q) pin_ctl_[DIIS_MAX + q] = order_[q];
+        DF_CUDA(cudaMemcpyAsync(d_ints_, pin_ctl_, sizeof(int) * 2 * DIIS_MAX, cudaMemcpyHostToDevice, s_));
+        diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, slot_, d_ints_, DIIS_MAX, d_B_);
+        DF_CHECK_LAUNCH();
+        const double* Fuse = h_->F.p;
+        if (it_ >= 2 && order_.size() >= 2) {
+            diis_solve_kernel<<<1, 1, 0, s_>>>(d_B_, d_ints_ + DIIS_MAX, (int)order_.size(), d_coef_,
+                                               d_ints_ + 2 * DIIS_MAX);
+            DF_CHECK_LAUNCH();
+            diis_combine_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->diisF.p, nn_, d_ints_ + DIIS_MAX, (int)order_.size(),
+                                                          d_coef_, h_->Fx.p);
+            DF_CHECK_LAUNCH();
+            Fuse = h_->Fx.p;
+        } else {
+            DF_CUDA(cudaMemsetAsync(d_ints_ + 2 * DIIS_MAX, 0, sizeof(int), s_));
+        }
+        roothaan(Fuse);
+    }
+
+    int status() const { return status_; }
+
+  private:
+    using clk = std::chrono::steady_clock;
 
     void eig(double* A, int m, double* w) {
         int lw = 0;
-        DF_SOLVER(cusolverDnDsyevd_bufferSize(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, &lw));
-        if (lw > lwork) {
-            if (work) cudaFree(work);
-            DF_CUDA(cudaMalloc((void**)&work, sizeof(double) * lw));
-            lwork = lw;
+        DF_SOLVER(cusolverDnDsyevd_bufferSize(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, &lw));
+        if (lw > lwork_) {
+            if (work_) cudaFree(work_);
+            work_ = nullptr;
+            DF_CUDA(cudaMalloc((void**)&work_, sizeof(double) * lw));
+            lwork_ = lw;
         }
-        DF_SOLVER(cusolverDnDsyevd(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, work, lwork, info));
-        int hinfo = 0;
-        DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        DF_CUDA(cudaStreamSynchronize(h->stream));
-        if (hinfo != 0) throw Error{DF_E_NUMERIC, "dsyevd failed, info " + std::to_string(hinfo)};
+        DF_SOLVER(cusolverDnDsyevd(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, work_,
+                                   lwork_, info_));
     }
-    ~Solver() {
-        if (work) cudaFree(work);
-        if (info) cudaFree(info);
+
+    // Fp = X^T F X ; eigenvectors ; C = X V ; dC = C_occ (n x nocc) ; D = 2 C_occ C_occ^T
+    void roothaan(const double* Fm) {
+        dgemm(s_, false, false, n_, nX_, n_, 1.0, Fm, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
+        eig(Fp_, nX_, h_->eps.p);
+        dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
+        DF_CUDA(cudaMemcpy2DAsync(h_->dC.p, sizeof(double) * nocc_, h_->C.p, sizeof(double) * nX_, sizeof(double) * nocc_,
+                                  n_, cudaMemcpyDeviceToDevice, s_));
+        dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
     }
+
+    void finish() {
+        done_ = true;
+        r_->converged = (status_ == DF_OK);
+        r_->status = status_;
+        r_->t_iter_s = std::chrono::duration<double>(clk::now() - t_iter_).count();
+        r_->t_jk_s = jk_ms_ / 1000.0;
+        r_->t_total_s = std::chrono::duration<double>(clk::now() - t_start_).count();
+    }
+
+    void release() {
+        if (work_) cudaFree(work_);
+        if (info_) cudaFree(info_);
+        if (d_ints_) cudaFree(d_ints_);
+        if (Fp_) cudaFree(Fp_);
+        if (T1_) cudaFree(T1_);
+        if (pin_) cudaFreeHost(pin_);
+        if (pin_ctl_) cudaFreeHost(pin_ctl_);
+        if (ev_done_) cudaEventDestroy(ev_done_);
+        if (ej0_) cudaEventDestroy(ej0_);
+        if (ej1_) cudaEventDestroy(ej1_);
+        work_ = nullptr;
+        info_ = nullptr;
+        d_ints_ = nullptr;
+        Fp_ = T1_ = nullptr;
+        pin_ = nullptr;
+        pin_ctl_ = nullptr;
+        ev_done_ = ej0_ = ej1_ = nullptr;
+    }
+
+    df_handle* h_;
+    df_options o_;
+    df_result* r_;
+    clk::time_point t_start_, t_iter_;
+    int n_ = 0, nocc_ = 0, nX_ = 0, dsize_ = 2, slices_ = 0, it_ = 0, slot_ = 0;
+    long long nn_ = 0;
+    cudaStream_t s_ = nullptr;
+    double* work_ = nullptr;
+    int lwork_ = 0;
+    int* info_ = nullptr;
+    int* d_ints_ = nullptr;
+    double *d_B_ = nullptr, *d_scal_ = nullptr, *d_coef_ = nullptr, *Fp_ = nullptr, *T1_ = nullptr;
+    double* pin_ = nullptr;
+    int* pin_ctl_ = nullptr;
+    cudaEvent_t ev_done_ = nullptr, ej0_ = nullptr, ej1_ = nullptr;
+    std::vector<int> present_, order_;
+    double e_old_ = 0.0, jk_ms_ = 0.0;
+    bool done_ = false;
+    int status_ = DF_E_NOTCONV;
 };
 
 }  // namespace
 
 int scf_drive(df_handle* h, const df_options* o, df_result* r) {
-    using clk = std::chrono::steady_clock;
-    const auto t_start = clk::now();
-    *r = df_result{};
-    r->e_nuc = h->e_nuc;
-    if (!h->built) {
-        const auto t0 = clk::now();
-        build_B(h, o->screen_tau, false);
-        r->t_build_s = std::chrono::duration<double>(clk::now() - t0).count();
+    ScfRun run(h, o, r);
+    run.begin();
+    while (!run.done()) {
+        run.enqueue_iteration();
+        run.finish_iteration();
     }
-    const int n = h->n, nocc = h->nocc;
-    const long long nn = (long long)n * n;
-    cudaStream_t s = h->stream;
-    const int dsize = std::max(2, std::min(o->diis_size, DIIS_MAX));
-    Solver sol{h, n, 0};
-    DF_CUDA(cudaMalloc((void**)&sol.info, sizeof(int)));
+    return run.status();
+}
 
-    // --- orthogonaliser -------------------------------------------------------------------
-    h->work1.alloc(nn);
-    h->work2.alloc(nn);
-    h->work3.alloc(nn);
-    h->eps.alloc(n);
-    DF_CUDA(cudaMemcpyAsync(h->work1.p, h->S.p, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    sol.eig(h->work1.p, n, h->eps.p);
-    std::vector<double> sv(n);
-    DF_CUDA(cudaMemcpy(sv.data(), h->eps.p, n * sizeof(double), cudaMemcpyDeviceToHost));
-    int first = 0;
-    while (first < n && sv[first] <= 1e-7) ++first;
-    const int nX = n - first;
-    if (nX < nocc) throw Error{DF_E_NUMERIC, "orthogonal basis smaller than the occupied space"};
-    h->nX = nX;
-    h->ndrop = first;
-    r->n_dropped = first;
-    h->X.alloc((size_t)n * nX);
-    build_x_kernel<<<nblk((long long)n * nX), 256, 0, s>>>(h->work1.p, h->eps.p, n, first, nX, h->X.p);
-    DF_CHECK_LAUNCH();
-
-    h->F.alloc(nn);
-    h->Fx.alloc(nn);
-    h->Dm.alloc(nn);
-    h->C.alloc((size_t)n * nX);
-    DF_CUDA(cudaMemsetAsync(h->C.p, 0, sizeof(double) * n * nX, s));
-    DF_CUDA(cudaMemsetAsync(h->eps.p, 0, sizeof(double) * n, s));
-    ensure_jk_buffers(h, nocc);
-    h->diisF.alloc((size_t)DIIS_MAX * nn);
-    h->diisE.alloc((size_t)DIIS_MAX * nX * nX);
-    h->diisB.alloc(DIIS_MAX * DIIS_MAX + 4 + DIIS_MAX);   // B matrix | energies(3) + maxerr | coef
-    double* d_B = h->diisB.p;
-    double* d_scal = d_B + DIIS_MAX * DIIS_MAX;
-    double* d_coef = d_scal + 4;
-    int* d_ints = nullptr;   // present[DIIS_MAX] | slots[DIIS_MAX] | status
-    DF_CUDA(cudaMalloc((void**)&d_ints, sizeof(int) * (2 * DIIS_MAX + 1)));
-    double* Fp = nullptr;    // X^T F X and its eigenvectors (nX x nX)
-    DF_CUDA(cudaMalloc((void**)&Fp, sizeof(double) * nX * nX));
-    double* T1 = nullptr;    // n x nX scratch
-    DF_CUDA(cudaMalloc((void**)&T1, sizeof(double) * n * nX));
-
-    auto roothaan = [&](const double* Fm) {
-        // Fp = X^T F X ; eigenvectors ; C = X V ; D = 2 Cocc Cocc^T ; dC = Cocc (n x nocc)
-        dgemm(s, false, false, n, nX, n, 1.0, Fm, n, h->X.p, nX, 0.0, T1, nX);
-        dgemm(s, true, false, nX, nX, n, 1.0, h->X.p, nX, T1, nX, 0.0, Fp, nX);
-        sol.eig(Fp, nX, h->eps.p);
-        dgemm(s, false, true, n, nX, nX, 1.0, h->X.p, nX, Fp, nX, 0.0, h->C.p, nX);
-        DF_CUDA(cudaMemcpy2DAsync(h->dC.p, sizeof(double) * nocc, h->C.p, sizeof(double) * nX, sizeof(double) * nocc, n,
-                                  cudaMemcpyDeviceToDevice, s));
-        dgemm(s, false, true, n, n, nocc, 2.0, h->dC.p, nocc, h->dC.p, nocc, 0.0, h->Dm.p, n);
-    };
-
-    int status = DF_E_NOTCONV;
+// Many molecules in lock-step: each iteration enqueues every unfinished molecule's work on its own
+// stream before waiting on any of them, so kernels of different molecules overlap on the GPU.
+int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs) {
+    std::vector<std::unique_ptr<ScfRun>> runs;
+    for (int i = 0; i < nmol; ++i) {
+        hs[i]->sync_timing = false;
+        runs.emplace_back(new ScfRun(hs[i], o, &rs[i]));
+    }
+    int status = DF_OK;
     try {
-        roothaan(h->H.p);   // core-Hamiltonian guess
-        std::vector<int> present(DIIS_MAX, 0), order;
-        std::vector<double> hs(4);
-        double e_old = 0.0;
-        double jk_ms = 0.0;
-        cudaEvent_t ej0, ej1;
-        DF_CUDA(cudaEventCreate(&ej0));
-        DF_CUDA(cudaEventCreate(&ej1));
-        const auto t_iter = clk::now();
-        int it = 0;
-        int slices = o->slices;   // split mode: o->slices early, SPLIT_LATE_SLICES once max|e| < SPLIT_RAMP_ERR
-        for (it = 1; it <= o->max_iter; ++it) {
-            DF_CUDA(cudaEventRecord(ej0, s));
-            jk_dispatch(h, h->Dm.p, h->dC.p, nocc, h->dJ.p, h->dK.p, o->precision, slices);
-            DF_CUDA(cudaEventRecord(ej1, s));
-            fock_kernel<<<nblk(nn), 256, 0, s>>>(h->H.p, h->dJ.p, h->dK.p, nn, h->F.p);
-            DF_CHECK_LAUNCH();
-            energy_kernel<<<1, 1024, 0, s>>>(h->Dm.p, h->H.p, h->dJ.p, h->dK.p, nn, d_scal);
-            DF_CHECK_LAUNCH();
-            // error vector e = X^T (FDS - SDF) X
-            dgemm(s, false, false, n, n, n, 1.0, h->F.p, n, h->Dm.p, n, 0.0, h->work1.p, n);
-            dgemm(s, false, false, n, n, n, 1.0, h->work1.p, n, h->S.p, n, 0.0, h->work2.p, n);
-            antisym_kernel<<<nblk(nn), 256, 0, s>>>(h->work2.p, n, h->work3.p);
-            DF_CHECK_LAUNCH();
-            dgemm(s, false, false, n, nX, n, 1.0, h->work3.p, n, h->X.p, nX, 0.0, T1, nX);
-            // write e into the next DIIS slot directly
-            int slot = 0;
-            if ((int)order.size() < dsize) {
-                while (present[slot]) ++slot;
-            } else {
-                slot = order.front();
-                order.erase(order.begin());
-                present[slot] = 0;
-            }
-            double* Eslot = h->diisE.p + (long long)slot * nX * nX;
-            dgemm(s, true, false, nX, nX, n, 1.0, h->X.p, nX, T1, nX, 0.0, Eslot, nX);
-            absmax_kernel<<<1, 1024, 0, s>>>(Eslot, (long long)nX * nX, d_scal + 3);
-            DF_CHECK_LAUNCH();
-            DF_CUDA(cudaMemcpyAsync(hs.data(), d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            DF_CUDA(cudaStreamSynchronize(s));
-            jk_ms += elapsed_ms(ej0, ej1);
-            const double energy = hs[0] + 0.5 * hs[1] - 0.5 * hs[2] + h->e_nuc;
-            const double err = hs[3];
-            if (!std::isfinite(energy) || !std::isfinite(err)) {
-                status = DF_E_NUMERIC;
-                break;
-            }
-            r->energy = energy;
-            r->e_one = hs[0];
-            r->e_coul = 0.5 * hs[1];
-            r->e_exch = -0.5 * hs[2];
-            r->last_err = err;
-            r->last_dE = (it > 1) ? energy - e_old : 0.0;
-            r->iterations = it;
-            const bool late_ready = o->precision != DF_PREC_SPLIT || slices >= SPLIT_LATE_SLICES;
-            if (it > 1 && late_ready && std::fabs(energy - e_old) < o->conv_E && err < o->conv_err) {
-                status = DF_OK;
-                break;
-            }
-            bool ramp = false;
-            if (o->precision == DF_PREC_SPLIT && slices < SPLIT_LATE_SLICES && err < SPLIT_RAMP_ERR) {
-                slices = SPLIT_LATE_SLICES;
-                r->ramp_iteration = it + 1;
-                ramp = true;
-            }
-            e_old = energy;
-            // DIIS bookkeeping: store F, dots, solve, combine. At the precision ramp the subspace is
-            // restarted from the current Fock matrix: the earlier ones carry the coarser exchange.
-            if (ramp) {
-                for (int q : order) present[q] = 0;
-                order.clear();
-            }
-            DF_CUDA(cudaMemcpyAsync(h->diisF.p + (long long)slot * nn, h->F.p, nn * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, s));
-            present[slot] = 1;
-            order.push_back(slot);
-            DF_CUDA(cudaMemcpyAsync(d_ints, present.data(), sizeof(int) * DIIS_MAX, cudaMemcpyHostToDevice, s));
-            diis_dots_kernel<<<DIIS_MAX, 256, 0, s>>>(h->diisE.p, (long long)nX * nX, slot, d_ints, DIIS_MAX, d_B);
-            DF_CHECK_LAUNCH();
-            const double* Fuse = h->F.p;
-            while (it >= 2 && order.size() >= 2) {
-                DF_CUDA(cudaMemcpyAsync(d_ints + DIIS_MAX, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s));
-                diis_solve_kernel<<<1, 1, 0, s>>>(d_B, d_ints + DIIS_MAX, (int)order.size(), d_coef, d_ints + 2 * DIIS_MAX);
-                DF_CHECK_LAUNCH();
-                int st = 0;
-                DF_CUDA(cudaMemcpyAsync(&st, d_ints + 2 * DIIS_MAX, sizeof(int), cudaMemcpyDeviceToHost, s));
-                DF_CUDA(cudaStreamSynchronize(s));
-                if (st == 0) {
-                    diis_combine_kernel<<<nblk(nn), 256, 0, s>>>(h->diisF.p, nn, d_ints + DIIS_MAX, (int)order.size(), d_coef,
-                                                                h->Fx.p);
-                    DF_CHECK_LAUNCH();
-                    Fuse = h->Fx.p;
-                    break;
+        for (auto& r : runs) r->begin();
+        bool active = true;
+        while (active) {
+            active = false;
+            for (auto& r : runs)
+                if (!r->done()) r->enqueue_iteration();
+            for (auto& r : runs)
+                if (!r->done()) {
+                    r->finish_iteration();
+                    active = active || !r->done();
                 }
-                present[order.front()] = 0;   // ill-conditioned: drop the oldest vector and retry
-                order.erase(order.begin());
-            }
-            roothaan(Fuse);
         }
-        if (it > o->max_iter) r->iterations = o->max_iter;
-        r->t_iter_s = std::chrono::duration<double>(clk::now() - t_iter).count();
-        r->t_jk_s = jk_ms / 1000.0;
-        cudaEventDestroy(ej0);
-        cudaEventDestroy(ej1);
+        for (auto& r : runs)
+            if (r->status() != DF_OK && status == DF_OK) status = r->status();
     } catch (...) {
-        cudaFree(d_ints);
-        cudaFree(Fp);
-        cudaFree(T1);
+        for (int i = 0; i < nmol; ++i) hs[i]->sync_timing = true;
         throw;
     }
-    cudaFree(d_ints);
-    cudaFree(Fp);
-    cudaFree(T1);
-    r->converged = (status == DF_OK);
-    r->status = status;
-    r->t_total_s = std::chrono::duration<double>(clk::now() - t_start).count();
+    for (int i = 0; i < nmol; ++i) hs[i]->sync_timing = true;
     return status;
 }
 

@@ -577,11 +577,13 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         default: run_split<5>(h, st, dC, nocc, dK, ev); break;
     }
     DF_CUDA(cudaEventRecord(e1, h->stream));
-    DF_CUDA(cudaEventSynchronize(e1));
-    h->timings_ms[8] = elapsed_ms(e0, e1);
-    h->timings_ms[9] = elapsed_ms(ev[0], ev[1]);    // Y = B C (split)
-    h->timings_ms[10] = elapsed_ms(ev[2], ev[3]);   // K contraction (split)
-    h->timings_ms[11] = h->timings_ms[8] - h->timings_ms[9] - h->timings_ms[10];   // slicing, reduce
+    if (h->sync_timing) {
+        DF_CUDA(cudaEventSynchronize(e1));
+        h->timings_ms[8] = elapsed_ms(e0, e1);
+        h->timings_ms[9] = elapsed_ms(ev[0], ev[1]);    // Y = B C (split)
+        h->timings_ms[10] = elapsed_ms(ev[2], ev[3]);   // K contraction (split)
+        h->timings_ms[11] = h->timings_ms[8] - h->timings_ms[9] - h->timings_ms[10];   // slicing, reduce
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (auto& e : ev) cudaEventDestroy(e);
