@@ -194,16 +194,21 @@ def gpu_arm(args):
             compare["fp64_s_per_iter"] = run_steps(binding.DF_PREC_FP64, 0, 1, 2)[0] / 1000.0
     lib.df_set_stream(h.h, None)
 
-    # time to a converged SCF from the core-Hamiltonian guess (B already built: its build time is added)
+    # time to a converged SCF from the core-Hamiltonian guess (B already built: its build time is added),
+    # and from the learned guess (network trained beforehand on smaller clusters; training not timed)
     ttc = {}
     scf_info = {}
+    learned = None
     if args.ttc:
-        runs = [("split" if split else "fp64", prec)]
+        runs = [("split" if split else "fp64", prec, None)]
+        if args.learned > 0:
+            learned, D0, t_guess = learned_guess(binding, clusters, h, args.learned)
+            runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess)))
         if split and args.compare_ttc:
-            runs.append(("fp64", binding.DF_PREC_FP64))
-        for label, p in runs:
-            res = h.scf(precision=p, slices=3)
-            ttc[label] = t_build + res["t_total_s"]
+            runs.append(("fp64", binding.DF_PREC_FP64, None))
+        for label, p, g in runs:
+            res = h.scf(precision=p, slices=3, guess=None if g is None else g[0])
+            ttc[label] = t_build + res["t_total_s"] + (0.0 if g is None else g[1])
             scf_info[label] = {"energy": res["energy"], "iterations": res["iterations"],
                                "converged": bool(res["converged"]), "t_iter_s": res["t_iter_s"],
                                "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"]}
@@ -272,6 +277,7 @@ def gpu_arm(args):
                     "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
         "time_to_converge_s": ttc or None, "scf": scf_info or None,
         "batched": batched,
+        "learned_guess": learned,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
@@ -280,6 +286,40 @@ def gpu_arm(args):
         print(json.dumps(line))
     if ws > 1:
         tdist.destroy_process_group()
+
+
+def learned_guess(binding, clusters, h, n_train):
+    """Train the density-guess network on converged densities of `n_train` seeded clusters (3-8
+    waters, seeds 10000+, generated by this library's FP64 SCF), then predict the guess for the
+    benchmark cluster. Returns (summary, D0, seconds to produce D0)."""
+    rng = clusters.SplitMix64(9090)
+    sizes = [3 + min(5, int(rng.uniform() * 6)) for _ in range(n_train)]
+    t0 = time.perf_counter()
+    X, Y = [], []
+    for k, w in enumerate(sizes):
+        s = clusters.water_cluster(w, 10000 + k)
+        with binding.Handle(s) as hh:
+            hh.scf()
+            Y.append(hh.water_blocks(hh.matrix("D")))
+        X.append(binding.water_features(s))
+    t_data = time.perf_counter() - t0
+    X, Y = np.concatenate(X), np.concatenate(Y)
+    nout = Y.shape[1]
+    net = binding.Mlp(binding.DF_MLP_NFEAT, 256, 3, nout, seed=7)
+    p = net.params()
+    p[-nout:] = Y.mean(axis=0)
+    p[-nout - nout * 256:-nout] = 0.0
+    net.set_params(p)
+    t0 = time.perf_counter()
+    hist = net.train(X, Y, epochs=200, batch=16, lr=3e-4, seed=3)
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    D0 = h.mlp_guess(net, bf16=True)
+    t_guess = time.perf_counter() - t0
+    net.close()
+    return ({"train_clusters": n_train, "train_waters": int(sum(sizes)), "network": "57-256x3-1275 ReLU, FP32 "
+             "weights, BF16 inference", "epochs": 200, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+             "t_data_s": t_data, "t_train_s": t_train, "t_guess_s": t_guess}, D0, t_guess)
 
 
 def batched_measure(binding, clusters, count, torch):
@@ -392,6 +432,7 @@ def main():
     ap.add_argument("--compare-ttc", action="store_true", help="also time a full FP64 SCF (minutes)")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false")
     ap.add_argument("--batch", type=int, default=16, help="molecules in the batched-SCF measurement (0: skip)")
+    ap.add_argument("--learned", type=int, default=24, help="training clusters for the learned guess (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -131,6 +131,48 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out);
  * molecule i's result; the return value is DF_OK if all converged, else the first failing status. */
 int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out);
 
+/* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
+ * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric
+ * (eigenvectors of X^T S D0 S X). Otherwise as scf_run. */
+int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_result* out);
+
+/* ---- learned initial guess (the paper has no counterpart; the build's design) -------------------
+ * Waters only: atoms as consecutive (O, H, H) triples, every water with the same basis. Each water's
+ * frame: origin O, z along the H-O-H bisector, x along H1 - H2. A network maps DF_MLP_NFEAT
+ * rotation-invariant features of the water's environment to the upper triangle of its diagonal density
+ * block in that frame; blocks are rotated to the laboratory frame with real-solid-harmonic rotation
+ * matrices and assembled block-diagonally. */
+#define DF_MLP_NFEAT 57
+typedef struct df_mlp df_mlp;
+
+/* Fully connected network nin -> nhidden (x nlayers, ReLU) -> nout, FP32 weights, He-initialised from
+ * `seed`; parameters live on the current device. */
+int df_mlp_create(int nin, int nhidden, int nlayers, int nout, unsigned long long seed, df_mlp** out);
+void df_mlp_free(df_mlp* m);
+/* Number of parameters; layout per layer l: W_l (out x in, row-major) then b_l. */
+long long df_mlp_nparams(const df_mlp* m);
+/* Copy parameters to (set = 0) or from (set = 1, also resets the Adam state) a host float array. */
+int df_mlp_params(df_mlp* m, float* host, int set);
+/* Mean-squared-error loss over ns samples (X: ns x nin, Y: ns x nout, host) and its gradient with
+ * respect to every parameter (host, nparams floats), by the GPU forward and backward kernels. */
+int df_mlp_gradients(df_mlp* m, const float* X, const float* Y, int ns, float* grad, float* loss);
+/* Adam training (lr, beta1 0.9, beta2 0.999) with shuffled minibatches (seeded); loss_history
+ * (epochs floats, may be NULL) receives each epoch's mean batch loss. */
+int df_mlp_train(df_mlp* m, const float* X, const float* Y, int ns, int epochs, int batch, float lr,
+                 unsigned long long seed, float* loss_history);
+/* Network outputs for ns samples (host arrays); bf16 = 1 runs BF16 weights and activations with FP32
+ * accumulation, 0 the FP32 network. */
+int df_mlp_predict(df_mlp* m, const float* X, int ns, int bf16, float* Y);
+/* Features of every water (out: nwater x DF_MLP_NFEAT); returns DF_MLP_NFEAT or a DF_E_* code. */
+int df_water_features(const df_atom* atoms, int natom, float* out);
+/* Upper triangles of each water's diagonal block of D (host, n x n) in the water's frame
+ * (out: nwater x nb(nb+1)/2 floats, nb = functions per water). */
+int df_water_blocks(df_handle* h, const double* D, float* out);
+/* D0 (host n x n) assembled from frame blocks (nwater x nb(nb+1)/2). */
+int df_water_density(df_handle* h, const float* blocks, double* D0);
+/* Learned D0 (host n x n) for the handle's water cluster with network m (bf16 = BF16 inference). */
+int df_mlp_guess(df_handle* h, df_mlp* m, int bf16, double* D0);
+
 /* Per-iteration record of the last scf_run: up to max_rows rows of 6 doubles
  * (iteration, energy, energy change, max|X^T(FDS - SDF)X|, exchange slices (0 = FP64), J/K build ms).
  * Returns the number of rows the run produced (which may exceed max_rows), or a negative DF_E_*. */

@@ -17,7 +17,10 @@ DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
-            "df_coulomb_noalloc", "df_scf_history", "scf_run_batch"]
+            "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
+            "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
+            "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess"]
+DF_MLP_NFEAT = 57
 
 
 class Atom(ctypes.Structure):
@@ -77,6 +80,21 @@ def load(path: str | None = None):
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
+    L.scf_run_guess.argtypes = [c_void_p, P(Options), dp, P(Result)]
+    fp = P(ctypes.c_float)
+    L.df_mlp_create.argtypes = [c_int, c_int, c_int, c_int, ctypes.c_ulonglong, P(c_void_p)]
+    L.df_mlp_free.argtypes = [c_void_p]
+    L.df_mlp_free.restype = None
+    L.df_mlp_nparams.argtypes = [c_void_p]
+    L.df_mlp_nparams.restype = ctypes.c_longlong
+    L.df_mlp_params.argtypes = [c_void_p, fp, c_int]
+    L.df_mlp_gradients.argtypes = [c_void_p, fp, fp, c_int, fp, fp]
+    L.df_mlp_train.argtypes = [c_void_p, fp, fp, c_int, c_int, c_int, ctypes.c_float, ctypes.c_ulonglong, fp]
+    L.df_mlp_predict.argtypes = [c_void_p, fp, c_int, c_int, fp]
+    L.df_water_features.argtypes = [P(Atom), c_int, fp]
+    L.df_water_blocks.argtypes = [c_void_p, dp, fp]
+    L.df_water_density.argtypes = [c_void_p, fp, dp]
+    L.df_mlp_guess.argtypes = [c_void_p, c_void_p, c_int, dp]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -165,13 +183,37 @@ class Handle:
         self._check(load().df_coulomb_noalloc(self.h, D_ptr, J_ptr), "df_coulomb_noalloc")
 
     def scf(self, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
-            incremental=0, screen_tau=0.0):
+            incremental=0, screen_tau=0.0, guess=None):
+        """SCF from the core-Hamiltonian guess, or from the natural orbitals of `guess` (n x n)."""
         o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau)
         r = Result()
-        rc = load().scf_run(self.h, ctypes.byref(o), ctypes.byref(r))
+        if guess is None:
+            rc = load().scf_run(self.h, ctypes.byref(o), ctypes.byref(r))
+        else:
+            g = np.ascontiguousarray(guess, dtype=np.float64)
+            rc = load().scf_run_guess(self.h, ctypes.byref(o), _dp(g), ctypes.byref(r))
         if rc not in (DF_OK, DF_E_NOTCONV):
             self._check(rc, "scf_run")
         return r.as_dict()
+
+    def water_blocks(self, D):
+        """Each water's diagonal block of D in its own frame (upper triangles, float32)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        nbw = water_nbf(self.system)
+        out = np.empty((len(self.system.atoms) // 3, nbw * (nbw + 1) // 2), dtype=np.float32)
+        self._check(load().df_water_blocks(self.h, _dp(D), _fp(out)), "df_water_blocks")
+        return out
+
+    def water_density(self, blocks):
+        blocks = np.ascontiguousarray(blocks, dtype=np.float32)
+        D0 = np.empty((self.n, self.n))
+        self._check(load().df_water_density(self.h, _fp(blocks), _dp(D0)), "df_water_density")
+        return D0
+
+    def mlp_guess(self, mlp, bf16=True):
+        D0 = np.empty((self.n, self.n))
+        self._check(load().df_mlp_guess(self.h, mlp.m, int(bf16), _dp(D0)), "df_mlp_guess")
+        return D0
 
     def history(self):
         """Per-iteration rows of the last SCF: iteration, energy, dE, max|e|, slices, J/K ms."""
@@ -235,6 +277,86 @@ def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, p
     if rc not in (DF_OK, DF_E_NOTCONV):
         raise DFError(rc, "scf_run_batch: " + load().df_last_error(handles[0].h).decode())
     return [out[i].as_dict() for i in range(n)]
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def water_nbf(system) -> int:
+    return int((2 * system.basis["l"][system.basis["atom"] < 3] + 1).sum())
+
+
+def water_features(system):
+    atoms = _atoms(system.atoms)
+    nw = len(system.atoms) // 3
+    out = np.empty((nw, DF_MLP_NFEAT), dtype=np.float32)
+    rc = load().df_water_features(atoms, len(system.atoms), _fp(out))
+    if rc < 0:
+        raise DFError(rc, "df_water_features")
+    return out
+
+
+class Mlp:
+    """The density-guess network (df_mlp_*): FP32 weights on the GPU, own training/inference kernels."""
+
+    def __init__(self, nin, nhidden, nlayers, nout, seed=0):
+        m = ctypes.c_void_p()
+        rc = load().df_mlp_create(nin, nhidden, nlayers, nout, seed, ctypes.byref(m))
+        if rc != DF_OK:
+            raise DFError(rc, "df_mlp_create")
+        self.m = m
+        self.nin, self.nout = nin, nout
+        self.nparams = load().df_mlp_nparams(m)
+
+    def params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        load().df_mlp_params(self.m, _fp(out), 0)
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        rc = load().df_mlp_params(self.m, _fp(p), 1)
+        if rc != DF_OK:
+            raise DFError(rc, "df_mlp_params")
+
+    def gradients(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        rc = load().df_mlp_gradients(self.m, _fp(X), _fp(Y), X.shape[0], _fp(g), _fp(loss))
+        if rc != DF_OK:
+            raise DFError(rc, "df_mlp_gradients")
+        return float(loss[0]), g
+
+    def train(self, X, Y, epochs, batch, lr, seed=0):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        hist = np.zeros(epochs, dtype=np.float32)
+        rc = load().df_mlp_train(self.m, _fp(X), _fp(Y), X.shape[0], epochs, batch, lr, seed, _fp(hist))
+        if rc != DF_OK:
+            raise DFError(rc, "df_mlp_train")
+        return hist
+
+    def predict(self, X, bf16=False):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((X.shape[0], self.nout), dtype=np.float32)
+        rc = load().df_mlp_predict(self.m, _fp(X), X.shape[0], int(bf16), _fp(Y))
+        if rc != DF_OK:
+            raise DFError(rc, "df_mlp_predict")
+        return Y
+
+    def close(self):
+        if getattr(self, "m", None):
+            load().df_mlp_free(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def estimate_bytes(system, precision=DF_PREC_FP64, slices=5) -> int:

@@ -176,7 +176,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
 void free_split(df_handle* h);
 
 // SCF (scf.cu)
-int scf_drive(df_handle* h, const df_options* o, df_result* r);
+int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess = nullptr);
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);

@@ -177,7 +177,8 @@ inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) /
 // own streams (scf_run_batch) while the GPU overlaps their kernels.
 class ScfRun {
   public:
-    ScfRun(df_handle* h, const df_options* o, df_result* r) : h_(h), o_(*o), r_(r) {}
+    ScfRun(df_handle* h, const df_options* o, df_result* r, const double* guess = nullptr)
+        : h_(h), o_(*o), r_(r), guess_(guess) {}
     ~ScfRun() { release(); }
 
     // orthogonaliser and core-Hamiltonian guess (synchronises: the dropped-eigenvalue count is needed)
@@ -244,7 +245,10 @@ class ScfRun {
         present_.assign(DIIS_MAX, 0);
         order_.clear();
         h_->history.clear();
-        roothaan(h_->H.p);   // core-Hamiltonian guess
+        if (guess_)
+            natural_orbitals(guess_);
+        else
+            roothaan(h_->H.p);   // core-Hamiltonian guess
         t_iter_ = clk::now();
         it_ = 0;
         done_ = false;
@@ -390,6 +394,23 @@ class ScfRun {
         dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
     }
 
+    // first orbitals from a guess density D0 (host): the nocc eigenvectors of X^T S D0 S X with the
+    // largest eigenvalues, C = X V_occ, D = 2 C C^T
+    void natural_orbitals(const double* D0) {
+        DF_CUDA(cudaMemcpyAsync(h_->work3.p, D0, nn_ * sizeof(double), cudaMemcpyHostToDevice, s_));
+        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->S.p, n_, h_->work3.p, n_, 0.0, h_->work1.p, n_);
+        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
+        dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work2.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
+        eig(Fp_, nX_, h_->eps.p);
+        dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
+        // ascending eigenvalues: the occupied natural orbitals are the last nocc columns
+        DF_CUDA(cudaMemcpy2DAsync(h_->dC.p, sizeof(double) * nocc_, h_->C.p + (nX_ - nocc_), sizeof(double) * nX_,
+                                  sizeof(double) * nocc_, n_, cudaMemcpyDeviceToDevice, s_));
+        dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
+        DF_CUDA(cudaStreamSynchronize(s_));   // D0 is host memory owned by the caller
+    }
+
     void finish() {
         done_ = true;
         r_->converged = (status_ == DF_OK);
@@ -422,6 +443,7 @@ class ScfRun {
     df_handle* h_;
     df_options o_;
     df_result* r_;
+    const double* guess_ = nullptr;
     clk::time_point t_start_, t_iter_;
     int n_ = 0, nocc_ = 0, nX_ = 0, dsize_ = 2, slices_ = 0, it_ = 0, slot_ = 0;
     long long nn_ = 0;
@@ -442,8 +464,8 @@ class ScfRun {
 
 }  // namespace
 
-int scf_drive(df_handle* h, const df_options* o, df_result* r) {
-    ScfRun run(h, o, r);
+int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess) {
+    ScfRun run(h, o, r, guess);
     run.begin();
     while (!run.done()) {
         run.enqueue_iteration();

@@ -15,7 +15,7 @@ def _declared():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names += re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+            names += re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

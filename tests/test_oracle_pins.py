@@ -424,3 +424,23 @@ def test_generator_counts_and_geometry():
         assert abs(r1 - 0.96) < 1e-12 and abs(r2 - 0.96) < 1e-12 and abs(ang - 104.5) < 1e-9
     # SplitMix64 reference values: seed 0 first output (published test vector)
     assert clusters.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+# --------------------------------------------------------------------------- learned-guess network
+
+def test_mlp_oracle_gradient_central_differences():
+    """The oracle's backpropagated gradient equals central differences of its own loss."""
+    from oracle import mlp
+    rs = np.random.default_rng(3)
+    dims = [5, 8, 8, 8, 4]
+    n = sum(a * b + b for a, b in zip(dims[:-1], dims[1:]))
+    p = rs.normal(size=n) * 0.5
+    X = rs.normal(size=(7, 5))
+    Y = rs.normal(size=(7, 4))
+    g = mlp.gradient(p, dims, X, Y)
+    h = 1e-6
+    for k in rs.choice(n, 40, replace=False):
+        e = np.zeros(n)
+        e[k] = h
+        fd = (mlp.loss(p + e, dims, X, Y) - mlp.loss(p - e, dims, X, Y)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 + 1e-6 * abs(g[k]), (k, fd, g[k])
