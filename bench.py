@@ -242,7 +242,10 @@ def gpu_arm(args):
         dom_y = avg["split_y_ms"] >= avg["split_k_ms"]
         achieved = y_tf if dom_y else k_tf
         pk = peaks.get("bf16_tflops")
-        roofline = {"kernel": ("y_split_kernel" if dom_y else "k_split_kernel") + " (BF16 mma.sync, Ozaki slices)",
+        tc = os.environ.get("DFHF_SPLIT_TC", "1") != "0" and S in (3, 5)
+        kname = ("ozaki_tc_kernel<Y>" if dom_y else "ozaki_tc_kernel<K>") + " (tcgen05 BF16, TMEM, TMA)" if tc else \
+            ("y_split_kernel" if dom_y else "k_split_kernel") + " (BF16 mma.sync)"
+        roofline = {"kernel": kname + ", Ozaki slices",
                     "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                     "frac": achieved / pk if pk else None,
                     "peak_source": f"{peak_src} bf16_tflops (cuBLAS burst)",

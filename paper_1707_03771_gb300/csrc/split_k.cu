@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -428,9 +429,26 @@ __global__ void k_split_reduce_kernel(const float2* __restrict__ Kpart, int nspl
 
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// tcgen05 kernels for the split products (3 and 5 slices); DFHF_SPLIT_TC=0 selects the mma.sync kernels
+bool use_tensor_cores() {
+    const char* v = std::getenv("DFHF_SPLIT_TC");
+    return !(v && v[0] == '0');
+}
+
 }  // namespace
 
+void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux, int np,
+                int ldy, float2* Y, int* err);
+void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
+                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
+void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K);
+
 struct SplitState {
+    // tensor-core (tcgen05) path
+    int* err = nullptr;          // device error word of the tcgen05 kernels
+    int2* tiles128 = nullptr;    // lower 128-tile pairs
+    float2* Kpart_tc = nullptr;  // [nsplit_tc][npt][npt]
+    int npt = 0, ntiles128 = 0, nsplit_tc = 0;
     int S = 0;
     int np = 0;
     bf16* Bs = nullptr;
@@ -457,6 +475,9 @@ void free_split(df_handle* h) {
     cudaFree(st->Ys);
     cudaFree(st->Ye);
     cudaFree(st->Kpart);
+    cudaFree(st->err);
+    cudaFree(st->tiles128);
+    cudaFree(st->Kpart_tc);
     delete st;
     h->split = nullptr;
 }
@@ -488,10 +509,15 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const size_t smem = (size_t)2 * S * (64 + BN) * LDS * sizeof(bf16) + (64 + BN) * sizeof(int);
     DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 gy(np / 64, naux, (ldy + BN - 1) / BN);
+    const bool tc = use_tensor_cores() && (S == 3 || S == 5);
     DF_CUDA(cudaEventRecord(ev[0], s));
-    y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np, ldy,
-                                                 st->Y);
-    DF_CHECK_LAUNCH();
+    if (tc) {
+        y_split_tc(s, S, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err);
+    } else {
+        y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np,
+                                                     ldy, st->Y);
+        DF_CHECK_LAUNCH();
+    }
     DF_CUDA(cudaEventRecord(ev[1], s));
     const long long nblk = (naux + st->PB - 1) / st->PB;
     const long long ystr = (long long)naux * np * ldy;
@@ -502,13 +528,20 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
     DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
     DF_CUDA(cudaEventRecord(ev[2], s));
-    k_split_kernel<S><<<dim3(ntiles, st->nsplit), 2 * (64 / WNT) * 32, ksmem, s>>>(st->Ys, ystr, st->Ye, naux, np, ldy, st->PB,
-                                                                    st->nsplit, h->ktiles.p, st->Kpart);
-    DF_CHECK_LAUNCH();
-    DF_CUDA(cudaEventRecord(ev[3], s));
-    const long long nn = (long long)h->n * h->n;
-    k_split_reduce_kernel<<<nblocks(nn, 256), 256, 0, s>>>(st->Kpart, st->nsplit, np, h->n, dK);
-    DF_CHECK_LAUNCH();
+    if (tc) {
+        k_split_tc(s, S, st->Ys, st->Ye, naux, np, ldy, st->PB, st->nsplit_tc, st->tiles128, st->ntiles128,
+                   st->Kpart_tc, st->npt, st->err);
+        DF_CUDA(cudaEventRecord(ev[3], s));
+        k_tc_reduce(s, st->Kpart_tc, st->nsplit_tc, st->npt, h->n, dK);
+    } else {
+        k_split_kernel<S><<<dim3(ntiles, st->nsplit), 2 * (64 / WNT) * 32, ksmem, s>>>(
+            st->Ys, ystr, st->Ye, naux, np, ldy, st->PB, st->nsplit, h->ktiles.p, st->Kpart);
+        DF_CHECK_LAUNCH();
+        DF_CUDA(cudaEventRecord(ev[3], s));
+        const long long nn = (long long)h->n * h->n;
+        k_split_reduce_kernel<<<nblocks(nn, 256), 256, 0, s>>>(st->Kpart, st->nsplit, np, h->n, dK);
+        DF_CHECK_LAUNCH();
+    }
 }
 
 }  // namespace
@@ -569,7 +602,24 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         const long long nblk = (h->naux + st->PB - 1) / st->PB;
         DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * nblk * np));
         DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
+        // tcgen05 K: lower 128-tile pairs, split over auxiliary blocks to fill the GPU
+        if (!st->err) DF_CUDA(cudaMalloc((void**)&st->err, sizeof(int)));
+        const int nt128 = (int)((np + 127) / 128);
+        st->npt = nt128 * 128;
+        st->ntiles128 = nt128 * (nt128 + 1) / 2;
+        std::vector<int2> t128;
+        for (int I = 0; I < nt128; ++I)
+            for (int J = 0; J <= I; ++J) t128.push_back(make_int2(I, J));
+        cudaFree(st->tiles128);
+        st->tiles128 = nullptr;
+        DF_CUDA(cudaMalloc((void**)&st->tiles128, sizeof(int2) * t128.size()));
+        DF_CUDA(cudaMemcpy(st->tiles128, t128.data(), sizeof(int2) * t128.size(), cudaMemcpyHostToDevice));
+        st->nsplit_tc = std::max(1, std::min((4 * 152 + 2 * st->ntiles128 - 1) / (2 * st->ntiles128), (int)nblk));
+        cudaFree(st->Kpart_tc);
+        st->Kpart_tc = nullptr;
+        DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * st->nsplit_tc * (long long)st->npt * st->npt));
     }
+    if (st->err) DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
     switch (slices) {
         case 2: run_split<2>(h, st, dC, nocc, dK, ev); break;
         case 3: run_split<3>(h, st, dC, nocc, dK, ev); break;
@@ -577,6 +627,13 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         default: run_split<5>(h, st, dC, nocc, dK, ev); break;
     }
     DF_CUDA(cudaEventRecord(e1, h->stream));
+    if (st->err) {
+        // the tcgen05 kernels bound their waits and report expiry here
+        int herr = 0;
+        DF_CUDA(cudaMemcpyAsync(&herr, st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        DF_CUDA(cudaStreamSynchronize(h->stream));
+        if (herr) throw Error{DF_E_TIMEOUT, "tensor-core exchange kernel timed out waiting on a barrier"};
+    }
     if (h->sync_timing) {
         DF_CUDA(cudaEventSynchronize(e1));
         h->timings_ms[8] = elapsed_ms(e0, e1);

@@ -1,0 +1,499 @@
+// Split-precision exchange on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// Same arithmetic as split_k.cu (Ozaki slices, exact 512-element FP32 chunks, float-float drains), with
+// the products issued as tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in tensor memory):
+//   * one CTA owns an output tile of 128 rows x N columns; every Ozaki level L = s + t (0-based) has
+//     its own FP32 accumulator of N columns in TMEM (S levels, S * N <= 512 columns);
+//   * a producer thread streams K-steps of 64 elements with TMA (3-D tensor maps, 128-byte swizzle):
+//     one step = slice s of the A tile (128 x 64) and the B slices t < S - s (N x 64 each), into a ring of
+//     shared-memory slots guarded by mbarriers;
+//   * one thread issues the MMAs (4 k16 instructions per step and B slice) and commits each slot back
+//     to the producer; at every chunk boundary it commits to the epilogue and waits until TMEM is free;
+//   * four epilogue warps (one per 32 TMEM lanes) read the level sums with tcgen05.ld, scale them by the
+//     exact power of two 2^{e_row + e_col - 7 (L + 2)} and add them into per-thread float-float rows.
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel records DF_E_TIMEOUT in a flag,
+// releases its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace dfhf {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TM = 128;            // output rows per CTA (TMEM lanes)
+constexpr int KS = 64;             // K elements per pipeline step (one 128-byte swizzle row)
+constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks
+constexpr int NSLOT = 3;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------------------------------------
+// PTX helpers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the error flag set) if the barrier did not complete within the budget
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES || *(volatile int*)err) {
+            atomicExch(err, DF_E_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(const void* tile) {
+    const unsigned a = smem_u32(tile);
+    uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused with 128-byte swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                  // swizzle: 128 bytes
+    return d;
+}
+
+// instruction descriptor: kind::f16, A and B BF16 (K-major), D FP32, M x N
+__host__ __device__ constexpr unsigned instr_desc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t a, uint64_t b, unsigned idesc, unsigned accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return e < -126 ? 0.f : __int_as_float((127 + min(e, 127)) << 23); }
+
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += err;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Work description. MODE 0 (Y = B C): CTA = (P, mu-tile, n-tile); K runs over nu (np), exponents
+// constant (row: Be[P][mu], column: Ce[i]). MODE 1 (K = sum Y Y^T): CTA = (lower tile pair, half,
+// split); K runs over auxiliary rows P in [p0, p1) and, inside each, over i (ldy, 64-steps), with one
+// chunk per block of PB rows (exponents Ye[block][mu], Ye[block][nu]).
+// ------------------------------------------------------------------------------------------------
+struct TcArgs {
+    int mode;
+    int naux, np, ldy, PB, nsplit;
+    const int* row_e;        // MODE 0: Be [naux][np]; MODE 1: Ye [nblk][np]
+    const int* col_e;        // MODE 0: Ce [ldy]
+    const int2* tiles;       // MODE 1: lower 128-tile pairs
+    float2* out;             // MODE 0: Y [naux][np][ldy]; MODE 1: Kpart [nsplit][npt][npt]
+    int npt;                 // MODE 1: padded dimension of Kpart (multiple of 128)
+    int* err;
+};
+
+template <int S, int N, int MODE>
+__global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                          const __grid_constant__ CUtensorMap mapB, TcArgs args) {
+    constexpr int A_BYTES = TM * KS * 2;          // 16 KB
+    constexpr int B_BYTES = N * KS * 2;
+    constexpr int SLOT = ((A_BYTES + S * B_BYTES) + 1023) / 1024 * 1024;
+    constexpr int NCOLS = S * N <= 32 ? 32 : (S * N <= 64 ? 64 : (S * N <= 128 ? 128 : (S * N <= 256 ? 256 : 512)));
+    static_assert(S * N <= 512, "TMEM holds at most 512 accumulator columns");
+    constexpr unsigned IDESC = instr_desc(TM, N);
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + NSLOT * SLOT);
+    uint64_t* empty = full + NSLOT;
+    uint64_t* acc_full = empty + NSLOT;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* mma_done = acc_empty + 1;
+    unsigned* tmem_slot = (unsigned*)(mma_done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* err = args.err;
+
+    // ---- work decode -------------------------------------------------------------------------
+    int P = 0, m0 = 0, n0 = 0, split = 0;
+    int2 IJ = make_int2(0, 0);
+    int nsteps = 0;          // pipeline steps = K-steps x S
+    int ksteps = 0;
+    int p0 = 0, p1 = 0, kpp = 0;
+    if (MODE == 0) {
+        const int mt = (args.np + TM - 1) / TM;
+        const int nt = args.ldy / N;
+        int b = blockIdx.x;
+        const int ntile = b % nt;
+        b /= nt;
+        m0 = (b % mt) * TM;
+        P = b / mt;
+        n0 = ntile * N;
+        ksteps = args.np / KS;
+    } else {
+        const int halves = TM / N;
+        int b = blockIdx.x;
+        const int h = b % halves;
+        b /= halves;
+        split = b % args.nsplit;
+        IJ = args.tiles[b / args.nsplit];
+        m0 = IJ.x * TM;
+        n0 = IJ.y * TM + h * N;
+        const int nblk = (args.naux + args.PB - 1) / args.PB;
+        const int b0 = (int)((long long)nblk * split / args.nsplit), b1 = (int)((long long)nblk * (split + 1) / args.nsplit);
+        p0 = b0 * args.PB;
+        p1 = min(args.naux, b1 * args.PB);
+        kpp = (args.ldy + KS - 1) / KS;
+        ksteps = (p1 - p0) * kpp;
+    }
+    nsteps = ksteps * S;
+
+    // ---- set-up: barriers (thread 0), tensor memory (warp 0) ------------------------------------
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 128);
+        mbar_init(mma_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    // chunk index of K-step ks (MODE 0: 8 steps; MODE 1: PB auxiliary rows)
+    auto chunk_of = [&](int ks) { return MODE == 0 ? ks / CHUNK_STEPS : (ks / kpp) / args.PB; };
+    const int nchunks = ksteps > 0 ? chunk_of(ksteps - 1) + 1 : 0;
+
+    if (warp == 4) {
+        // ---------------------------------- producer ------------------------------------------
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapA) : "memory");
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapB) : "memory");
+            int issued = 0;
+            for (int it = 0; it < nsteps; ++it) {
+                const int slot = it % NSLOT;
+                if (!mbar_wait(&empty[slot], ((it / NSLOT) & 1) ^ 1, err)) break;
+                const int ks = it / S, s = it % S;
+                const int nb = S - s;
+                mbar_expect_tx(&full[slot], A_BYTES + nb * B_BYTES);
+                unsigned char* base = smem + slot * SLOT;
+                if (MODE == 0) {
+                    const int kx = ks * KS;
+                    tma_load_3d(base, &mapA, kx, m0, s * args.naux + P, &full[slot]);
+                    for (int t = 0; t < nb; ++t) tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t, &full[slot]);
+                } else {
+                    const int Pr = p0 + ks / kpp, kx = (ks % kpp) * KS;
+                    tma_load_3d(base, &mapA, kx, m0, s * args.naux + Pr, &full[slot]);
+                    for (int t = 0; t < nb; ++t)
+                        tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t * args.naux + Pr, &full[slot]);
+                }
+                ++issued;
+            }
+            // copies in flight complete before the kernel may leave: wait (bounded) for the last slots
+            if (*(volatile int*)err)
+                for (int it = max(0, issued - NSLOT); it < issued; ++it) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[it % NSLOT], (it / NSLOT) & 1) && clock64() - t0 < WAIT_CYCLES) {
+                    }
+                }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------- MMA issuer ----------------------------------------
+        if (lane == 0) {
+            int chunk = 0;
+            bool ok = true;
+            for (int it = 0; it < nsteps && ok; ++it) {
+                const int ks = it / S, s = it % S;
+                const int c = chunk_of(ks);
+                if (s == 0 && c != chunk) {       // new chunk: hand the finished sums to the epilogue
+                    mma_commit(acc_full);
+                    ok = mbar_wait(acc_empty, (chunk & 1), err);
+                    fence_after();
+                    chunk = c;
+                    if (!ok) break;
+                }
+                const int slot = it % NSLOT;
+                if (!mbar_wait(&full[slot], (it / NSLOT) & 1, err)) break;
+                fence_after();
+                unsigned char* base = smem + slot * SLOT;
+                const bool first_in_chunk = (s == 0) && (ks == 0 || chunk_of(ks - 1) != c);
+#pragma unroll
+                for (int k = 0; k < KS / 16; ++k) {
+                    const uint64_t ad = smem_desc(base) + (uint64_t)(k * 2);   // +32 bytes per k16
+                    for (int t = 0; t < S - s; ++t) {
+                        const uint64_t bd = smem_desc(base + A_BYTES + t * B_BYTES) + (uint64_t)(k * 2);
+                        mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, IDESC, (first_in_chunk && k == 0) ? 0u : 1u);
+                    }
+                }
+                mma_commit(&empty[slot]);
+            }
+            if (ok && nsteps > 0) mma_commit(acc_full);
+            // every MMA this thread issued has completed before tensor memory is released
+            mma_commit(mma_done);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < WAIT_CYCLES) {
+            }
+        }
+    } else {
+        // ---------------------------------- epilogue (warps 0-3) ------------------------------
+        // MODE 0: exponents are the same for every chunk, so chunk sums are accumulated with the level
+        // factor 2^{-7(L+2)} only and the row/column powers of two are applied once at the end.
+        const int row = warp * 32 + lane;               // TMEM lane = tile row
+        const int grow = m0 + row;
+        float hi[N], lo[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) hi[c] = lo[c] = 0.f;
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        for (int ch = 0; ch < nchunks; ++ch) {
+            int erow = 0;
+            int ce[MODE == 1 ? N : 1];
+            if (MODE == 1) {
+                const long long blk = p0 / args.PB + ch;
+                erow = (grow < args.np) ? args.row_e[blk * args.np + grow] : 0;
+#pragma unroll
+                for (int c = 0; c < (MODE == 1 ? N : 1); ++c)
+                    ce[c] = (n0 + c < args.np) ? __ldg(args.row_e + blk * args.np + n0 + c) : 0;
+            }
+            if (!mbar_wait(acc_full, ch & 1, err)) break;
+            fence_after();
+#pragma unroll 1
+            for (int L = S - 1; L >= 0; --L) {
+                const float lev = pow2f(-7 * (L + 2));
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(lane_base + (unsigned)(L * N + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float sc = (MODE == 1) ? pow2f(erow + ce[(c0 + j) % (MODE == 1 ? N : 1)] - 7 * (L + 2)) : lev;
+                        two_sum_acc(hi[c0 + j], lo[c0 + j], v[j] * sc);
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive(acc_empty);
+        }
+        // output
+        if (!*(volatile int*)err && grow < args.np) {
+            if (MODE == 0) {
+                const int er = args.row_e[(long long)P * args.np + grow];
+                float2* o = args.out + ((long long)P * args.np + grow) * args.ldy + n0;
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    const float f = pow2f(er + __ldg(args.col_e + n0 + c));
+                    o[c] = make_float2(hi[c] * f, lo[c] * f);
+                }
+            } else {
+                float2* o = args.out + ((long long)split * args.npt + grow) * args.npt + n0;
+#pragma unroll
+                for (int c = 0; c < N; ++c) o[c] = make_float2(hi[c], lo[c]);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOLS));
+}
+
+template <int S, int N>
+size_t tc_smem_bytes() {
+    constexpr int SLOT = ((TM * KS * 2 + S * N * KS * 2) + 1023) / 1024 * 1024;
+    return (size_t)NSLOT * SLOT + 1024 + 256;
+}
+
+// ------------------------------------------------------------------------------------------------
+// tensor maps through the driver entry point (no link-time dependence on libcuda)
+// ------------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        DF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) throw Error{DF_E_CUDA, "cuTensorMapEncodeTiled unavailable"};
+        fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 3-D BF16 tensor [d2][d1][d0] (d0 contiguous) with box {64, rows, 1}, 128-byte swizzle, zero fill
+CUtensorMap make_map(const bf16* base, unsigned long long d0, unsigned long long d1, unsigned long long d2,
+                     unsigned rows) {
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)KS, rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{DF_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
+    return m;
+}
+
+template <int S, int N, int MODE>
+void launch_tc(cudaStream_t s, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, unsigned grid) {
+    const size_t smem = tc_smem_bytes<S, N>();
+    DF_CUDA(cudaFuncSetAttribute(ozaki_tc_kernel<S, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ozaki_tc_kernel<S, N, MODE><<<grid, 192, smem, s>>>(a, b, args);
+    DF_CHECK_LAUNCH();
+}
+
+// K[mu][nu] (n x n, FP64) = sum over splits of the float pairs, read from the computed lower 128-tiles
+__global__ void k_tc_reduce_kernel(const float2* __restrict__ Kpart, int nsplit, int npt, int n, double* __restrict__ K) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int a = (int)(idx / n), b = (int)(idx % n);
+    if (a / TM < b / TM) {
+        const int t = a;
+        a = b;
+        b = t;
+    }
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) {
+        const float2 v = Kpart[((long long)q * npt + a) * npt + b];
+        s += (double)v.x + (double)v.y;
+    }
+    K[idx] = s;
+}
+
+}  // namespace
+
+void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K) {
+    const long long nn = (long long)n * n;
+    k_tc_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Kpart, nsplit, npt, n, K);
+    DF_CHECK_LAUNCH();
+}
+
+// Y[P][mu][i] (float pairs) = B_P C from the slices Bs [S][naux][np][np], Cs [S][ldy][np]
+void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux, int np,
+                int ldy, float2* Y, int* err) {
+    constexpr int N = 80;
+    if (ldy % 32) throw Error{DF_E_ARG, "tensor-core split Y: occupied width must be a multiple of 32"};
+    TcArgs a{};
+    a.mode = 0;
+    a.naux = naux;
+    a.np = np;
+    a.ldy = ldy;
+    a.row_e = Be;
+    a.col_e = Ce;
+    a.out = Y;
+    a.err = err;
+    const CUtensorMap ma = make_map(Bs, np, np, (unsigned long long)S * naux, TM);
+    const unsigned mt = (np + TM - 1) / TM;
+    if (ldy % N == 0) {
+        const CUtensorMap mb = make_map(Cs, np, ldy, S, N);
+        const unsigned grid = (unsigned)naux * mt * (ldy / N);
+        switch (S) {
+            case 3: launch_tc<3, N, 0>(s, ma, mb, a, grid); break;
+            case 5: launch_tc<5, N, 0>(s, ma, mb, a, grid); break;
+            default: throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices"};
+        }
+    } else {
+        constexpr int N2 = 32;
+        const CUtensorMap mb = make_map(Cs, np, ldy, S, N2);
+        const unsigned grid = (unsigned)naux * mt * (ldy / N2);
+        switch (S) {
+            case 3: launch_tc<3, N2, 0>(s, ma, mb, a, grid); break;
+            case 5: launch_tc<5, N2, 0>(s, ma, mb, a, grid); break;
+            default: throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices"};
+        }
+    }
+}
+
+// K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs)
+void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
+                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
+    constexpr int N = 64;
+    TcArgs a{};
+    a.mode = 1;
+    a.naux = naux;
+    a.np = np;
+    a.ldy = ldy;
+    a.PB = PB;
+    a.nsplit = nsplit;
+    a.row_e = Ye;
+    a.tiles = tiles128;
+    a.out = Kpart;
+    a.npt = npt;
+    a.err = err;
+    const CUtensorMap ma = make_map(Ys, ldy, np, (unsigned long long)S * naux, TM);
+    const CUtensorMap mb = make_map(Ys, ldy, np, (unsigned long long)S * naux, N);
+    const unsigned grid = (unsigned)ntiles * nsplit * (TM / N);
+    switch (S) {
+        case 3: launch_tc<3, N, 1>(s, ma, mb, a, grid); break;
+        case 5: launch_tc<5, N, 1>(s, ma, mb, a, grid); break;
+        default: throw Error{DF_E_ARG, "tensor-core split K supports 3 or 5 slices"};
+    }
+}
+
+}  // namespace dfhf

@@ -1,0 +1,49 @@
+"""The tcgen05 (TMEM + TMA) split-precision kernels against the mma.sync split kernels and the FP64
+path on the same B and C. Both split paths form the same exact integer chunk sums, so they agree to
+the FP64 rounding of their final sums."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1707_03771_gb300 import clusters
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1707_03771_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def _k(h, lib, D, C, slices, tc):
+    old = os.environ.get("DFHF_SPLIT_TC")
+    os.environ["DFHF_SPLIT_TC"] = "1" if tc else "0"
+    try:
+        return h.jk(D, C, lib.DF_PREC_SPLIT, slices)[1]
+    finally:
+        if old is None:
+            del os.environ["DFHF_SPLIT_TC"]
+        else:
+            os.environ["DFHF_SPLIT_TC"] = old
+
+
+@pytest.mark.parametrize("name", ["water2", "water8"])
+@pytest.mark.parametrize("slices", [3, 5])
+def test_tensor_core_split_matches_mma_sync_and_fp64(lib, name, slices):
+    system = clusters.workload(name)
+    rng = np.random.default_rng(12)
+    with lib.Handle(system) as h:
+        h.build_B()
+        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+        D = 2 * C @ C.T
+        K64 = h.jk(D, C, lib.DF_PREC_FP64)[1]
+        Kms = _k(h, lib, D, C, slices, tc=False)
+        Ktc = _k(h, lib, D, C, slices, tc=True)
+        Ktc2 = _k(h, lib, D, C, slices, tc=True)
+    scale = np.abs(K64).max()
+    assert np.array_equal(Ktc, Ktc2)
+    assert np.abs(Ktc - Kms).max() <= 1e-12 * scale, np.abs(Ktc - Kms).max() / scale
+    assert np.abs(Ktc - K64).max() <= 2.0 ** (7 - 7 * slices) * scale
