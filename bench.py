@@ -41,6 +41,27 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(value, device=None):
+    """The largest `value` over all ranks of the process group (a replicated job takes as long as its
+    slowest replica); `value` itself when no group is initialised or it has one rank."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_members(count, rank):
+    """The clusters of one rank's batched-SCF measurement: `count` (waters, seed) pairs, sizes drawn
+    uniformly from 1-8 waters, seeds 1000 + rank * count + k, so replicas solve disjoint molecule sets of
+    the same size distribution (weak scaling: the work per GPU does not change with the rank count)."""
+    from paper_1707_03771_gb300 import clusters
+    rng = clusters.SplitMix64(4242 + rank)
+    return [(1 + min(7, int(rng.uniform() * 8)), 1000 + rank * count + k) for k in range(count)]
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -161,11 +182,7 @@ def gpu_arm(args):
             per.append(dict(h.timings()))
         ev1.record(stream)
         torch.cuda.synchronize()
-        total = ev0.elapsed_time(ev1)
-        if ws > 1:
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(ev0.elapsed_time(ev1), dev)
         return total / steps, per
 
     with ClockSampler(local) as clocks:
@@ -179,11 +196,7 @@ def gpu_arm(args):
     t1 = time.perf_counter()
     for _ in range(args.steps):
         Jh, Kh = h.jk(D, C, prec, S)
-    e2e_s = (time.perf_counter() - t1) / args.steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t1) / args.steps, dev)
     lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
 
     # comparisons: the other precisions on the same density
@@ -214,8 +227,8 @@ def gpu_arm(args):
                                "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"]}
 
     batched = None
-    if args.batch > 0 and rank == 0:
-        batched = batched_measure(binding, clusters, args.batch, torch)
+    if args.batch > 0:
+        batched = batched_measure(binding, clusters, args.batch, torch, rank, dev)
 
     peaks, peak_src = _peaks()
     keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
@@ -325,12 +338,12 @@ def learned_guess(binding, clusters, h, n_train):
              "t_data_s": t_data, "t_train_s": t_train, "t_guess_s": t_guess}, D0, t_guess)
 
 
-def batched_measure(binding, clusters, count, torch):
-    """Many small clusters (sizes drawn uniformly from 1-8 waters, seeds 1000+): time to converge all of
-    them with the split-precision SCF, one after another versus together (scf_run_batch in waves)."""
-    rng = clusters.SplitMix64(4242)
-    sizes = [1 + min(7, int(rng.uniform() * 8)) for _ in range(count)]
-    systems = [clusters.water_cluster(w, 1000 + k) for k, w in enumerate(sizes)]
+def batched_measure(binding, clusters, count, torch, rank=0, dev=None):
+    """Many small clusters (batch_members): time to converge all of them with the split-precision SCF,
+    one after another versus together (scf_run_batch in waves); times are the maximum over ranks."""
+    members = batch_members(count, rank)
+    sizes = [w for w, _ in members]
+    systems = [clusters.water_cluster(w, seed) for w, seed in members]
     prec = binding.DF_PREC_SPLIT
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -339,12 +352,12 @@ def batched_measure(binding, clusters, count, torch):
         with binding.Handle(s) as h:
             seq.append(h.scf(precision=prec, slices=3))
     torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+    t_seq = max_over_ranks(time.perf_counter() - t0, dev)
     free, _ = torch.cuda.mem_get_info()
     t0 = time.perf_counter()
     res = binding.scf_waves(systems, int(0.5 * free), precision=prec, slices=3)
     torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    t_batch = max_over_ranks(time.perf_counter() - t0, dev)
     de = max(abs(a["energy"] - b["energy"]) for a, b in zip(seq, res))
     return {"molecules": count, "waters": sizes, "basis_functions": int(sum(s.nbf for s in systems)),
             "t_sequential_s": t_seq, "t_batched_s": t_batch, "speedup": t_seq / t_batch,

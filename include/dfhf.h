@@ -68,7 +68,11 @@ typedef struct {
     int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..5) in early iterations;
                                 once max|e| < 1e-4 the exchange is built with 5 slices, and the SCF
                                 converges only on those builds */
-    int incremental;         /* 1: late iterations build K from the density change (split mode) */
+    int incremental;         /* 1: late iterations (split: from the 5-slice ramp; FP64: once max|e| < 1e-4)
+                                build K = K[D_ref] + K[D - D_ref], the change factorised exactly from the
+                                occupied orbitals of both densities (QR of [C, C_ref], 2 nocc x 2 nocc
+                                eigenproblem) and built at 3 slices; D_ref is rebuilt in full every 8
+                                iterations. 0: every iteration builds K in full. */
     double screen_tau;       /* drop shell triples whose bound is below tau (0 = none) */
 } df_options;
 
@@ -85,6 +89,7 @@ typedef struct {
     int status;              /* DF_OK or DF_E_NOTCONV / DF_E_NUMERIC */
     int n_dropped;           /* orbitals removed by canonical orthogonalisation */
     int ramp_iteration;      /* split mode: first iteration built with 5 slices (0 if never) */
+    int incremental_builds;  /* iterations whose K was K[D_ref] + K[D - D_ref] (options.incremental) */
     double t_build_s;        /* df_build_B time within this call (0 if B was already built) */
     double t_iter_s;         /* total SCF iteration time */
     double t_jk_s;           /* time in J/K builds */

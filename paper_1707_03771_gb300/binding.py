@@ -43,7 +43,7 @@ class Result(ctypes.Structure):
                 ("e_coul", ctypes.c_double), ("e_exch", ctypes.c_double), ("last_dE", ctypes.c_double),
                 ("last_err", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("ramp_iteration", ctypes.c_int),
-                ("t_build_s", ctypes.c_double),
+                ("incremental_builds", ctypes.c_int), ("t_build_s", ctypes.c_double),
                 ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double)]
 
     def as_dict(self):
@@ -267,11 +267,11 @@ class Handle:
 
 
 def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
-              screen_tau=0.0):
+              screen_tau=0.0, incremental=0):
     """Solve several molecules together (scf_run_batch); returns one result dict per handle."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[hd.h.value for hd in handles])
-    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, 0, screen_tau)
+    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau)
     out = (Result * n)()
     rc = load().scf_run_batch(hs, n, ctypes.byref(o), out)
     if rc not in (DF_OK, DF_E_NOTCONV):

@@ -190,6 +190,17 @@ void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, dou
         exchange_fp64(h, nocc, dK);
 }
 
+// K alone for m columns of occupied-like coefficients dC (n x m, device), FP64 or split
+void exchange_only(df_handle* h, const double* dC, int m, int precision, int slices, double* dK) {
+    ensure_jk_buffers(h, m);
+    if (precision == DF_PREC_SPLIT) {
+        exchange_split(h, dC, m, slices, dK);
+    } else {
+        pad_occupied(h, dC, m, ((m + 31) / 32) * 32);
+        exchange_fp64(h, m, dK);
+    }
+}
+
 }  // namespace dfhf
 
 using namespace dfhf;

@@ -4,6 +4,9 @@
 //   core-Hamiltonian guess, F = H + J - K, E = tr(DH) + 1/2 tr(DJ) - 1/2 tr(DK) + E_nuc,
 //   Pulay DIIS on e = X^T (F D S - S D F) X, Roothaan step X^T F X = V eps V^T, C = X V,
 //   D = 2 C_occ C_occ^T (Aufbau), converged when |dE| < conv_E and max|e| < conv_err.
+// DIIS works in the orthogonal basis: with F' = X^T F X and C = X V (so C^T S X = V^T), the error is
+// e = 2 (F' P - P F') with P = V_occ V_occ^T, the extrapolation combines the F' of earlier iterations,
+// and only the occupied orbitals C_occ = X V_occ are formed each iteration.
 // Every step runs on the device in FP64 (DIIS included); only the energy and max|e| cross to the
 // host each iteration for the convergence test. The symmetric eigensolver is cuSOLVER's dsyevd.
 #include <algorithm>
@@ -19,12 +22,15 @@ namespace dfhf {
 void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
                  int slices);
 void build_B(df_handle* h, double tau, bool keep);
+void exchange_only(df_handle* h, const double* dC, int m, int precision, int slices, double* dK);
 
 namespace {
 
 constexpr int DIIS_MAX = 16;
 constexpr int SPLIT_LATE_SLICES = 5;      // slices of the late split-precision exchange builds
 constexpr double SPLIT_RAMP_ERR = 1e-4;   // max|e| below which the late builds start
+constexpr int INC_SLICES = 3;             // slices of the density-change exchange builds (split mode)
+constexpr int INC_RESET = 8;              // iterations per reference density (one full build, then changes)
 
 __global__ void build_x_kernel(const double* __restrict__ U, const double* __restrict__ s, int n, int first, int nX,
                                double* __restrict__ X) {
@@ -71,12 +77,12 @@ __global__ void energy_kernel(const double* __restrict__ D, const double* __rest
     }
 }
 
-// E1 = T - T^T (n x n)
-__global__ void antisym_kernel(const double* __restrict__ T, int n, double* __restrict__ E) {
+// E = a (T - T^T) (n x n)
+__global__ void antisym_kernel(const double* __restrict__ T, int n, double a, double* __restrict__ E) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const int i = (int)(idx / n), j = (int)(idx % n);
-    E[idx] = T[idx] - T[(long long)j * n + i];
+    E[idx] = a * (T[idx] - T[(long long)j * n + i]);
 }
 
 // out = max |x| (single block)
@@ -170,6 +176,54 @@ __global__ void diis_combine_kernel(const double* __restrict__ Fs, long long len
     Fx[i] = s;
 }
 
+// Incremental Fock build. With D = 2 C C^T and D_ref = 2 C_r C_r^T, the change is
+// (D - D_ref)/2 = W G W^T, W = [C, C_r] (n x 2m), G = diag(+1 (m), -1 (m)). With W = Q R (QR) and the
+// small eigenproblem R G R^T = Z L Z^T, (D - D_ref)/2 = sum_k l_k v_k v_k^T with v = Q Z; by Sylvester's
+// law of inertia at most m of the l_k are positive and m negative, so in ascending order the first m
+// carry the negative part and the last m the positive part. The exchange of the change is then
+// K[C_+] - K[C_-] with C_+- = v sqrt(max(+-l, 0)) (the exchange here is the orbital form, K[C] = sum_P
+// (B_P C)(B_P C)^T = sum_P B_P (D/2) B_P).
+
+// W (column-major n x 2m) = [C, C_r] from two row-major n x m blocks
+__global__ void assemble_w_kernel(const double* __restrict__ C, const double* __restrict__ Cr, int n, int m,
+                                  double* __restrict__ W) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * 2 * m) return;
+    const int j = (int)(idx / n), mu = (int)(idx % n);
+    W[idx] = j < m ? C[(long long)mu * m + j] : Cr[(long long)mu * m + (j - m)];
+}
+
+// core = R G R^T (2m x 2m, symmetric) from the upper triangle R of a column-major QR factor (lda n)
+__global__ void core_kernel(const double* __restrict__ W, int n, int m, double* __restrict__ core) {
+    const int m2 = 2 * m;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m2 * m2) return;
+    const int i = idx / m2, j = idx % m2;
+    double s = 0;
+    for (int k = max(i, j); k < m2; ++k) {
+        const double t = W[(long long)k * n + i] * W[(long long)k * n + j];
+        s += k < m ? t : -t;
+    }
+    core[idx] = s;
+}
+
+// Cm[mu][q] = v_q[mu] sqrt(max(-l_q, 0)), Cp[mu][q] = v_{m+q}[mu] sqrt(max(l_{m+q}, 0)); Vt rows are v_k
+__global__ void split_factors_kernel(const double* __restrict__ Vt, const double* __restrict__ lam, int n, int m,
+                                     double* __restrict__ Cp, double* __restrict__ Cm) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * m) return;
+    const int mu = (int)(idx / m), q = (int)(idx % m);
+    Cm[idx] = Vt[(long long)q * n + mu] * sqrt(fmax(-lam[q], 0.0));
+    Cp[idx] = Vt[(long long)(m + q) * n + mu] * sqrt(fmax(lam[m + q], 0.0));
+}
+
+// K = Kref + Kp - Km
+__global__ void k_update_kernel(const double* __restrict__ Kref, const double* __restrict__ Kp,
+                                const double* __restrict__ Km, long long len, double* __restrict__ K) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) K[i] = Kref[i] + Kp[i] - Km[i];
+}
+
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // One molecule's SCF as a sequence of asynchronous iterations with a single host synchronisation each
@@ -226,7 +280,6 @@ class ScfRun {
         build_x_kernel<<<nblk((long long)n_ * nX_), 256, 0, s_>>>(h_->work1.p, h_->eps.p, n_, first, nX_, h_->X.p);
         DF_CHECK_LAUNCH();
         h_->F.alloc(nn_);
-        h_->Fx.alloc(nn_);
         h_->Dm.alloc(nn_);
         h_->C.alloc((size_t)n_ * nX_);
         DF_CUDA(cudaMemsetAsync(h_->C.p, 0, sizeof(double) * n_ * nX_, s_));
@@ -242,13 +295,16 @@ class ScfRun {
         DF_CUDA(cudaMemsetAsync(d_ints_, 0, sizeof(int) * (2 * DIIS_MAX + 2), s_));
         DF_CUDA(cudaMalloc((void**)&Fp_, sizeof(double) * nX_ * nX_));
         DF_CUDA(cudaMalloc((void**)&T1_, sizeof(double) * n_ * nX_));
+        DF_CUDA(cudaMalloc((void**)&Fo_, sizeof(double) * nX_ * nX_));
         present_.assign(DIIS_MAX, 0);
         order_.clear();
         h_->history.clear();
-        if (guess_)
+        if (guess_) {
             natural_orbitals(guess_);
-        else
-            roothaan(h_->H.p);   // core-Hamiltonian guess
+        } else {
+            to_orth(h_->H.p, Fp_);   // core-Hamiltonian guess
+            solve_orth();
+        }
         t_iter_ = clk::now();
         it_ = 0;
         done_ = false;
@@ -260,18 +316,23 @@ class ScfRun {
     void enqueue_iteration() {
         ++it_;
         DF_CUDA(cudaEventRecord(ej0_, s_));
-        jk_dispatch(h_, h_->Dm.p, h_->dC.p, nocc_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+        if (o_.incremental && late_ && inc_since_ref_ >= 0 && inc_since_ref_ + 1 < INC_RESET) {
+            incremental_jk();
+            ++inc_since_ref_;
+            ++r_->incremental_builds;
+        } else {
+            jk_dispatch(h_, h_->Dm.p, h_->dC.p, nocc_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+            if (o_.incremental && late_) set_reference();
+        }
         DF_CUDA(cudaEventRecord(ej1_, s_));
         fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, h_->F.p);
         DF_CHECK_LAUNCH();
         energy_kernel<<<1, 1024, 0, s_>>>(h_->Dm.p, h_->H.p, h_->dJ.p, h_->dK.p, nn_, d_scal_);
         DF_CHECK_LAUNCH();
-        // error vector e = X^T (FDS - SDF) X, written into the next DIIS slot
-        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->F.p, n_, h_->Dm.p, n_, 0.0, h_->work1.p, n_);
-        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
-        antisym_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->work2.p, n_, h_->work3.p);
-        DF_CHECK_LAUNCH();
-        dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work3.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        // F' = X^T F X; error e = X^T (FDS - SDF) X = 2 (F' P - P F'), P = V_occ V_occ^T, into the next slot
+        to_orth(h_->F.p, Fo_);
+        dgemm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
+        dgemm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
         slot_ = 0;
         if ((int)order_.size() < dsize_) {
             while (present_[slot_]) ++slot_;
@@ -281,7 +342,8 @@ class ScfRun {
             present_[slot_] = 0;
         }
         double* Eslot = h_->diisE.p + (long long)slot_ * nX_ * nX_;
-        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Eslot, nX_);
+        antisym_kernel<<<nblk((long long)nX_ * nX_), 256, 0, s_>>>(h_->work1.p, nX_, 2.0, Eslot);
+        DF_CHECK_LAUNCH();
         absmax_kernel<<<1, 1024, 0, s_>>>(Eslot, (long long)nX_ * nX_, d_scal_ + 3);
         DF_CHECK_LAUNCH();
         DF_CUDA(cudaMemcpyAsync(pin_, d_scal_, 4 * sizeof(double), cudaMemcpyDeviceToHost, s_));
@@ -335,13 +397,15 @@ class ScfRun {
             r_->ramp_iteration = it_ + 1;
             ramp = true;
         }
+        if (!late_ && err < SPLIT_RAMP_ERR) late_ = true;
         // DIIS: at the precision ramp the subspace restarts from the current Fock matrix (the earlier
         // ones carry the coarser exchange)
         if (ramp) {
             for (int q : order_) present_[q] = 0;
             order_.clear();
         }
-        DF_CUDA(cudaMemcpyAsync(h_->diisF.p + (long long)slot_ * nn_, h_->F.p, nn_ * sizeof(double),
+        const long long no = (long long)nX_ * nX_;
+        DF_CUDA(cudaMemcpyAsync(h_->diisF.p + (long long)slot_ * no, Fo_, no * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s_));
         present_[slot_] = 1;
         order_.push_back(slot_);
@@ -350,19 +414,18 @@ class ScfRun {
         DF_CUDA(cudaMemcpyAsync(d_ints_, pin_ctl_, sizeof(int) * 2 * DIIS_MAX, cudaMemcpyHostToDevice, s_));
         diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, slot_, d_ints_, DIIS_MAX, d_B_);
         DF_CHECK_LAUNCH();
-        const double* Fuse = h_->F.p;
         if (it_ >= 2 && order_.size() >= 2) {
             diis_solve_kernel<<<1, 1, 0, s_>>>(d_B_, d_ints_ + DIIS_MAX, (int)order_.size(), d_coef_,
                                                d_ints_ + 2 * DIIS_MAX);
             DF_CHECK_LAUNCH();
-            diis_combine_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->diisF.p, nn_, d_ints_ + DIIS_MAX, (int)order_.size(),
-                                                          d_coef_, h_->Fx.p);
+            diis_combine_kernel<<<nblk(no), 256, 0, s_>>>(h_->diisF.p, no, d_ints_ + DIIS_MAX, (int)order_.size(),
+                                                         d_coef_, Fp_);
             DF_CHECK_LAUNCH();
-            Fuse = h_->Fx.p;
         } else {
             DF_CUDA(cudaMemsetAsync(d_ints_ + 2 * DIIS_MAX, 0, sizeof(int), s_));
+            DF_CUDA(cudaMemcpyAsync(Fp_, Fo_, no * sizeof(double), cudaMemcpyDeviceToDevice, s_));
         }
-        roothaan(Fuse);
+        solve_orth();
     }
 
     int status() const { return status_; }
@@ -370,27 +433,87 @@ class ScfRun {
   private:
     using clk = std::chrono::steady_clock;
 
-    void eig(double* A, int m, double* w) {
-        int lw = 0;
-        DF_SOLVER(cusolverDnDsyevd_bufferSize(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, &lw));
+    // the full build just enqueued becomes the reference: K_ref = K, C_ref = C_occ
+    void set_reference() {
+        if (!Kref_) {
+            const long long m = nocc_;
+            DF_CUDA(cudaMalloc((void**)&Kref_, sizeof(double) * nn_ * 3));   // K_ref | K_+ | K_-
+            DF_CUDA(cudaMalloc((void**)&Cref_, sizeof(double) * n_ * m * 3));   // C_ref | C_+ | C_-
+            DF_CUDA(cudaMalloc((void**)&Wq_, sizeof(double) * n_ * 2 * m * 2));   // W / Q | V^T
+            DF_CUDA(cudaMalloc((void**)&core_, sizeof(double) * (4 * m * m + 4 * m)));   // core | l | tau
+        }
+        DF_CUDA(cudaMemcpyAsync(Kref_, h_->dK.p, nn_ * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaMemcpyAsync(Cref_, h_->dC.p, sizeof(double) * n_ * nocc_, cudaMemcpyDeviceToDevice, s_));
+        inc_since_ref_ = 0;
+    }
+
+    // J in full; K = K_ref + K[C_+] - K[C_-] from the factorised density change
+    void incremental_jk() {
+        const int m = nocc_, m2 = 2 * nocc_;
+        ensure_jk_buffers(h_, nocc_);
+        coulomb_fp64(h_, h_->Dm.p, h_->dJ.p);
+        double* W = Wq_;
+        double* Vt = Wq_ + (long long)n_ * m2;
+        double* lam = core_ + (long long)m2 * m2;
+        double* tau = lam + m2;
+        double *Cp = Cref_ + (long long)n_ * m, *Cm = Cp + (long long)n_ * m;
+        double *Kp = Kref_ + nn_, *Km = Kp + nn_;
+        assemble_w_kernel<<<nblk((long long)n_ * m2), 256, 0, s_>>>(h_->dC.p, Cref_, n_, m, W);
+        DF_CHECK_LAUNCH();
+        int lw = 0, lw2 = 0;
+        DF_SOLVER(cusolverDnDgeqrf_bufferSize(h_->solver, n_, m2, W, n_, &lw));
+        DF_SOLVER(cusolverDnDorgqr_bufferSize(h_->solver, n_, m2, m2, W, n_, tau, &lw2));
+        grow_work(std::max(lw, lw2));
+        DF_SOLVER(cusolverDnDgeqrf(h_->solver, n_, m2, W, n_, tau, work_, lwork_, info_));
+        core_kernel<<<nblk((long long)m2 * m2), 256, 0, s_>>>(W, n_, m, core_);
+        DF_CHECK_LAUNCH();
+        DF_SOLVER(cusolverDnDorgqr(h_->solver, n_, m2, m2, W, n_, tau, work_, lwork_, info_));
+        eig(core_, m2, lam);
+        // V^T (2m x n): row k = sum_j Z[k][j] Q[:, j]; Q column-major n x 2m is the row-major 2m x n Q^T
+        dgemm(s_, false, false, m2, n_, m2, 1.0, core_, m2, W, n_, 0.0, Vt, n_);
+        split_factors_kernel<<<nblk((long long)n_ * m), 256, 0, s_>>>(Vt, lam, n_, m, Cp, Cm);
+        DF_CHECK_LAUNCH();
+        const int inc_slices = o_.precision == DF_PREC_SPLIT ? INC_SLICES : 0;
+        exchange_only(h_, Cp, m, o_.precision, inc_slices, Kp);
+        exchange_only(h_, Cm, m, o_.precision, inc_slices, Km);
+        k_update_kernel<<<nblk(nn_), 256, 0, s_>>>(Kref_, Kp, Km, nn_, h_->dK.p);
+        DF_CHECK_LAUNCH();
+    }
+
+    void grow_work(int lw) {
         if (lw > lwork_) {
             if (work_) cudaFree(work_);
             work_ = nullptr;
             DF_CUDA(cudaMalloc((void**)&work_, sizeof(double) * lw));
             lwork_ = lw;
         }
+    }
+
+    void eig(double* A, int m, double* w) {
+        int lw = 0;
+        DF_SOLVER(cusolverDnDsyevd_bufferSize(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, &lw));
+        grow_work(lw);
         DF_SOLVER(cusolverDnDsyevd(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, work_,
                                    lwork_, info_));
     }
 
-    // Fp = X^T F X ; eigenvectors ; C = X V ; dC = C_occ (n x nocc) ; D = 2 C_occ C_occ^T
-    void roothaan(const double* Fm) {
+    // Fo = X^T Fm X (nX x nX)
+    void to_orth(const double* Fm, double* Fo) {
         dgemm(s_, false, false, n_, nX_, n_, 1.0, Fm, n_, h_->X.p, nX_, 0.0, T1_, nX_);
-        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
+        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fo, nX_);
+    }
+
+    // Roothaan step on the orthogonal-basis Fock matrix held in Fp_: eigenvectors in place (row j of the
+    // row-major view is eigenvector j, ascending), the nocc lowest occupied
+    void solve_orth() {
         eig(Fp_, nX_, h_->eps.p);
-        dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
-        DF_CUDA(cudaMemcpy2DAsync(h_->dC.p, sizeof(double) * nocc_, h_->C.p, sizeof(double) * nX_, sizeof(double) * nocc_,
-                                  n_, cudaMemcpyDeviceToDevice, s_));
+        vt_ = Fp_;
+        occupy();
+    }
+
+    // dC = C_occ = X V_occ (n x nocc) from the occupied rows vt_ ; D = 2 C_occ C_occ^T
+    void occupy() {
+        dgemm(s_, false, true, n_, nocc_, nX_, 1.0, h_->X.p, nX_, vt_, nX_, 0.0, h_->dC.p, nocc_);
         dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
     }
 
@@ -403,15 +526,15 @@ class ScfRun {
         dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work2.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
         dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
         eig(Fp_, nX_, h_->eps.p);
-        dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
-        // ascending eigenvalues: the occupied natural orbitals are the last nocc columns
-        DF_CUDA(cudaMemcpy2DAsync(h_->dC.p, sizeof(double) * nocc_, h_->C.p + (nX_ - nocc_), sizeof(double) * nX_,
-                                  sizeof(double) * nocc_, n_, cudaMemcpyDeviceToDevice, s_));
-        dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
+        // ascending eigenvalues: the occupied natural orbitals are the last nocc eigenvectors
+        vt_ = Fp_ + (long long)(nX_ - nocc_) * nX_;
+        occupy();
         DF_CUDA(cudaStreamSynchronize(s_));   // D0 is host memory owned by the caller
     }
 
     void finish() {
+        // all orbitals of the last Roothaan step, C = X V
+        if (vt_ == Fp_) dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
         done_ = true;
         r_->converged = (status_ == DF_OK);
         r_->status = status_;
@@ -426,6 +549,12 @@ class ScfRun {
         if (d_ints_) cudaFree(d_ints_);
         if (Fp_) cudaFree(Fp_);
         if (T1_) cudaFree(T1_);
+        if (Fo_) cudaFree(Fo_);
+        if (Kref_) cudaFree(Kref_);
+        if (Cref_) cudaFree(Cref_);
+        if (Wq_) cudaFree(Wq_);
+        if (core_) cudaFree(core_);
+        Kref_ = Cref_ = Wq_ = core_ = nullptr;
         if (pin_) cudaFreeHost(pin_);
         if (pin_ctl_) cudaFreeHost(pin_ctl_);
         if (ev_done_) cudaEventDestroy(ev_done_);
@@ -434,7 +563,7 @@ class ScfRun {
         work_ = nullptr;
         info_ = nullptr;
         d_ints_ = nullptr;
-        Fp_ = T1_ = nullptr;
+        Fp_ = T1_ = Fo_ = nullptr;
         pin_ = nullptr;
         pin_ctl_ = nullptr;
         ev_done_ = ej0_ = ej1_ = nullptr;
@@ -452,7 +581,11 @@ class ScfRun {
     int lwork_ = 0;
     int* info_ = nullptr;
     int* d_ints_ = nullptr;
-    double *d_B_ = nullptr, *d_scal_ = nullptr, *d_coef_ = nullptr, *Fp_ = nullptr, *T1_ = nullptr;
+    double *d_B_ = nullptr, *d_scal_ = nullptr, *d_coef_ = nullptr, *Fp_ = nullptr, *T1_ = nullptr, *Fo_ = nullptr;
+    const double* vt_ = nullptr;   // occupied eigenvectors (nocc rows of length nX) of the last Roothaan step
+    double *Kref_ = nullptr, *Cref_ = nullptr, *Wq_ = nullptr, *core_ = nullptr;   // incremental Fock state
+    bool late_ = false;            // past the max|e| < 1e-4 point (split: the 5-slice builds)
+    int inc_since_ref_ = -1;       // density-change builds since the reference (-1: no reference yet)
     double* pin_ = nullptr;
     int* pin_ctl_ = nullptr;
     cudaEvent_t ev_done_ = nullptr, ej0_ = nullptr, ej1_ = nullptr;
