@@ -6,12 +6,17 @@
 #include <cstring>
 #include <new>
 
+#include <cstdlib>
+#include <string>
+
 #include "common.cuh"
 
 namespace dfhf {
 
 void rys_eval(const double* dT, int count, int n, double* dx, double* dw, cudaStream_t s);
 const double* rys_table_host();
+void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const double* Linv, const double* A,
+                  double* B);
 void whiten_float_float(cudaStream_t s, int m, long long ncol, const double* Linv, double* Lff, double* A, double* B,
                         long long ld, bool restore_a);
 
@@ -160,13 +165,25 @@ void build_B(df_handle* h, double tau, bool keep) {
     zero_upper_kernel<<<(unsigned)(((long long)na * na + 255) / 256), 256, 0, s>>>(h->Linv.p, na);
     DF_CHECK_LAUNCH();
     DF_CUDA(cudaEventRecord(ev[2], s));
-    h->B.alloc(rows);
-    {
+    const char* wenv = std::getenv("DFHF_WHITEN");
+    if (wenv && std::string(wenv) == "ff") {
+        // float-float whitening on the FP32 pipes (selectable for comparison)
+        h->B.alloc(rows);
         DevBuf<double> lff;
         lff.alloc((size_t)na * na);
         whiten_float_float(s, na, h->pk.row, h->Linv.p, lff.p, h->A3c.p, h->B.p, h->pk.row, keep);
         DF_CUDA(cudaStreamSynchronize(s));
         lff.release();
+    } else if (keep) {
+        h->B.alloc(rows);
+        whiten_ozaki(s, na, h->pk.row, h->pk.row, h->Linv.p, h->A3c.p, h->B.p);
+    } else {
+        // in place: the unwhitened tensor's memory becomes B
+        whiten_ozaki(s, na, h->pk.row, h->pk.row, h->Linv.p, h->A3c.p, h->A3c.p);
+        h->B.p = h->A3c.p;
+        h->B.n = h->A3c.n;
+        h->A3c.p = nullptr;
+        h->A3c.n = 0;
     }
     DF_CUDA(cudaEventRecord(ev[3], s));
     DF_CUDA(cudaEventSynchronize(ev[3]));

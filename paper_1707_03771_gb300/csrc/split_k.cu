@@ -20,6 +20,7 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace dfhf {
 
@@ -34,18 +35,6 @@ constexpr int SMAX = 5;
 
 // exact 2^e as a float; 0 below the normal range (such contributions are below 2^-126 of the scale)
 __device__ __forceinline__ float pow2f(int e) { return e < -126 ? 0.f : __int_as_float((127 + min(e, 127)) << 23); }
-
-// x (already scaled so |x| < 1) -> S integer slices
-template <int S>
-__device__ __forceinline__ void split_fp64(double x, bf16* out, long long stride) {
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const double t = x * 128.0;
-        const double m = rint(t);
-        x = t - m;
-        out[s * stride] = __float2bfloat16_rn((float)m);
-    }
-}
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     const float s = hi + v;

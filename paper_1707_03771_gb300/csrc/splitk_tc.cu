@@ -13,6 +13,12 @@
 //     exact power of two 2^{e_row + e_col - 7 (L + 2)} and add them into per-thread float-float rows.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records DF_E_TIMEOUT in a flag,
 // releases its tensor memory and returns.
+//
+// A third mode runs the metric whitening B = L^-1 A (paper eq. 1, third form) the same way with 7 slices:
+// A operand = slices of L^-1 rows (one exponent per auxiliary row), B operand = slices of the
+// transposed three-index columns (one exponent per pair column), K over the auxiliary index up to the
+// end of the lower triangle, exact 448-element chunks (7 slices: a level sum is below 9 * 2^12 per
+// term, 448 terms stay below 2^24), output in FP64.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -29,7 +35,8 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TM = 128;            // output rows per CTA (TMEM lanes)
 constexpr int KS = 64;             // K elements per pipeline step (one 128-byte swizzle row)
-constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks
+constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks (S <= 5)
+constexpr int CHUNK_STEPS_W = 7;   // 448-element exact chunks (whitening, S = 7)
 constexpr int NSLOT = 3;
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -142,6 +149,11 @@ struct TcArgs {
     float2* out;             // MODE 0: Y [naux][np][ldy]; MODE 1: Kpart [nsplit][npt][npt]
     int npt;                 // MODE 1: padded dimension of Kpart (multiple of 128)
     int* err;
+    // MODE 2 (whitening): rows = naux (np is set to naux), ncols pair columns of this chunk,
+    // row_e = L^-1 row exponents, col_e = column exponents, output FP64 rows of stride ldo
+    int ncols;
+    double* outd;
+    long long ldo;
 };
 
 template <int S, int N, int MODE>
@@ -152,7 +164,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     constexpr int SLOT = ((A_BYTES + S * B_BYTES) + 1023) / 1024 * 1024;
     constexpr int NCOLS = S * N <= 32 ? 32 : (S * N <= 64 ? 64 : (S * N <= 128 ? 128 : (S * N <= 256 ? 256 : 512)));
     static_assert(S * N <= 512, "TMEM holds at most 512 accumulator columns");
-    constexpr unsigned IDESC = instr_desc(TM, N);
+    constexpr int MMA_SLICES = 256 / N;            // B slices per MMA (M = 128 allows N <= 256)
+    static_assert(N % 16 == 0 && N <= 256, "MMA width");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -182,6 +195,11 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         P = b / mt;
         n0 = ntile * N;
         ksteps = args.np / KS;
+    } else if (MODE == 2) {
+        const int ntn = args.ncols / N;
+        m0 = (blockIdx.x / ntn) * TM;             // row-tile major: the L^-1 tile is shared in L2
+        n0 = (blockIdx.x % ntn) * N;
+        ksteps = (min(args.naux, m0 + TM) + KS - 1) / KS;   // L^-1 is lower triangular
     } else {
         const int halves = TM / N;
         int b = blockIdx.x;
@@ -221,8 +239,10 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     fence_after();
     const unsigned tmem = *tmem_slot;
 
-    // chunk index of K-step ks (MODE 0: 8 steps; MODE 1: PB auxiliary rows)
-    auto chunk_of = [&](int ks) { return MODE == 0 ? ks / CHUNK_STEPS : (ks / kpp) / args.PB; };
+    // chunk index of K-step ks (MODE 0: 8 steps; MODE 1: PB auxiliary rows; MODE 2: 7 steps)
+    auto chunk_of = [&](int ks) {
+        return MODE == 0 ? ks / CHUNK_STEPS : (MODE == 2 ? ks / CHUNK_STEPS_W : (ks / kpp) / args.PB);
+    };
     const int nchunks = ksteps > 0 ? chunk_of(ksteps - 1) + 1 : 0;
 
     if (warp == 4) {
@@ -241,6 +261,10 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 if (MODE == 0) {
                     const int kx = ks * KS;
                     tma_load_3d(base, &mapA, kx, m0, s * args.naux + P, &full[slot]);
+                    for (int t = 0; t < nb; ++t) tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t, &full[slot]);
+                } else if (MODE == 2) {
+                    const int kx = ks * KS;
+                    tma_load_3d(base, &mapA, kx, m0, s, &full[slot]);
                     for (int t = 0; t < nb; ++t) tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t, &full[slot]);
                 } else {
                     const int Pr = p0 + ks / kpp, kx = (ks % kpp) * KS;
@@ -278,12 +302,17 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 fence_after();
                 unsigned char* base = smem + slot * SLOT;
                 const bool first_in_chunk = (s == 0) && (ks == 0 || chunk_of(ks - 1) != c);
+                // the B slices t < S - s are consecutive N-row tiles in shared memory and their levels
+                // s + t consecutive N-column accumulators in TMEM, so up to 256 / N of them form one MMA
+                // of width cnt * N (one read of the A tile per MMA instead of one per slice)
 #pragma unroll
                 for (int k = 0; k < KS / 16; ++k) {
                     const uint64_t ad = smem_desc(base) + (uint64_t)(k * 2);   // +32 bytes per k16
-                    for (int t = 0; t < S - s; ++t) {
+                    for (int t = 0; t < S - s; t += MMA_SLICES) {
+                        const int cnt = min(MMA_SLICES, S - s - t);
                         const uint64_t bd = smem_desc(base + A_BYTES + t * B_BYTES) + (uint64_t)(k * 2);
-                        mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, IDESC, (first_in_chunk && k == 0) ? 0u : 1u);
+                        mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, instr_desc(TM, cnt * N),
+                                 (first_in_chunk && k == 0) ? 0u : 1u);
                     }
                 }
                 mma_commit(&empty[slot]);
@@ -297,8 +326,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         }
     } else {
         // ---------------------------------- epilogue (warps 0-3) ------------------------------
-        // MODE 0: exponents are the same for every chunk, so chunk sums are accumulated with the level
-        // factor 2^{-7(L+2)} only and the row/column powers of two are applied once at the end.
+        // MODE 0 and 2: exponents are the same for every chunk, so chunk sums are accumulated with the
+        // level factor 2^{-7(L+2)} only and the row/column powers of two are applied once at the end.
         const int row = warp * 32 + lane;               // TMEM lane = tile row
         const int grow = m0 + row;
         float hi[N], lo[N];
@@ -307,26 +336,31 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
         for (int ch = 0; ch < nchunks; ++ch) {
             int erow = 0;
-            int ce[MODE == 1 ? N : 1];
+            long long blk = 0;
             if (MODE == 1) {
-                const long long blk = p0 / args.PB + ch;
+                blk = p0 / args.PB + ch;
                 erow = (grow < args.np) ? args.row_e[blk * args.np + grow] : 0;
-#pragma unroll
-                for (int c = 0; c < (MODE == 1 ? N : 1); ++c)
-                    ce[c] = (n0 + c < args.np) ? __ldg(args.row_e + blk * args.np + n0 + c) : 0;
             }
             if (!mbar_wait(acc_full, ch & 1, err)) break;
             fence_after();
-#pragma unroll 1
-            for (int L = S - 1; L >= 0; --L) {
-                const float lev = pow2f(-7 * (L + 2));
+            // per element the levels are added in descending order; column exponents (MODE 1) are read
+            // per 16-column group to keep them out of the register file
 #pragma unroll
-                for (int c0 = 0; c0 < N; c0 += 16) {
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                int ce[16];
+                if (MODE == 1) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        ce[j] = (n0 + c0 + j < args.np) ? __ldg(args.row_e + blk * args.np + n0 + c0 + j) : 0;
+                }
+#pragma unroll 1
+                for (int L = S - 1; L >= 0; --L) {
+                    const float lev = pow2f(-7 * (L + 2));
                     float v[16];
                     tmem_ld16(lane_base + (unsigned)(L * N + c0), v);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float sc = (MODE == 1) ? pow2f(erow + ce[(c0 + j) % (MODE == 1 ? N : 1)] - 7 * (L + 2)) : lev;
+                        const float sc = (MODE == 1) ? pow2f(erow + ce[j] - 7 * (L + 2)) : lev;
                         two_sum_acc(hi[c0 + j], lo[c0 + j], v[j] * sc);
                     }
                 }
@@ -336,7 +370,12 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         }
         // output
         if (!*(volatile int*)err && grow < args.np) {
-            if (MODE == 0) {
+            if (MODE == 2) {
+                const int er = args.row_e[grow];
+                double* o = args.outd + (long long)grow * args.ldo + n0;
+#pragma unroll
+                for (int c = 0; c < N; ++c) o[c] = ldexp((double)hi[c] + (double)lo[c], er + __ldg(args.col_e + n0 + c));
+            } else if (MODE == 0) {
                 const int er = args.row_e[(long long)P * args.np + grow];
                 float2* o = args.out + ((long long)P * args.np + grow) * args.ldy + n0;
 #pragma unroll
@@ -468,6 +507,29 @@ void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16
             default: throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices"};
         }
     }
+}
+
+// B[P][c] = sum_Q L^-1[P][Q] A[Q][c] for the ncols columns of one chunk, from the 7 slices
+// Ls [7][naux][kp] (row exponents eL) and At [7][ncols][kp] (column exponents eA); rows of `out` have
+// stride ldo. kp is naux padded to a multiple of 64 (zero slices beyond naux), ncols a multiple of 64.
+void whiten_tc(cudaStream_t s, const bf16* Ls, const int* eL, const bf16* At, const int* eA, int naux, int kp,
+               int ncols, double* out, long long ldo, int* err) {
+    constexpr int S = 7, N = 64;
+    if (kp % KS || ncols % N) throw Error{DF_E_ARG, "internal: whitening operands not padded to 64"};
+    TcArgs a{};
+    a.mode = 2;
+    a.naux = naux;
+    a.np = naux;
+    a.row_e = eL;
+    a.col_e = eA;
+    a.err = err;
+    a.ncols = ncols;
+    a.outd = out;
+    a.ldo = ldo;
+    const CUtensorMap ma = make_map(Ls, kp, naux, S, TM);
+    const CUtensorMap mb = make_map(At, kp, ncols, S, N);
+    const unsigned grid = (unsigned)((naux + TM - 1) / TM) * (unsigned)(ncols / N);
+    launch_tc<S, N, 2>(s, ma, mb, a, grid);
 }
 
 // K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs)
