@@ -9,9 +9,11 @@ split-precision form (BF16 Ozaki slices on the tensor cores) at the 5 slices the
 final iterations; --precision fp64 times the FP64 form. `value` is seconds per J/K build with inputs
 already on the device (CUDA events on the stream the library launches on, max over ranks); `e2e` is
 the same through the C ABI with host buffers (D and C_occ copied in, J and K copied out inside the
-timed region). `time_to_converge_s` is one full SCF (integrals + whitening + iterations) from the
-core-Hamiltonian guess to |dE| < 1e-10 Eh and max|FDS - SDF| < 1e-7; `compare` holds the per-iteration
-time of the early-iteration split form (3 slices) and of the FP64 form on the same density.
+timed region). `time_to_converge_s` is one full SCF (integrals + whitening + iterations) to
+|dE| < 1e-10 Eh and max|FDS - SDF| < 1e-7, from the core-Hamiltonian guess ("split") and from the
+learned guess ("split_learned"), both with incremental Fock builds late; "split_learned_full" repeats
+the learned run with full 5-slice builds. `compare` holds the per-iteration time of the early split
+form (3 slices) and of the FP64 form on the same density.
 
 Inputs (46.7 GB of B) are far larger than L2 (126 MB), so no flush is needed between steps.
 Under torchrun with N > 1 each rank runs an independent replica (the path has no exchange step).
@@ -213,18 +215,24 @@ def gpu_arm(args):
     scf_info = {}
     learned = None
     if args.ttc:
-        runs = [("split" if split else "fp64", prec, None)]
+        # split precision: S = 3 early, then a 5-slice reference K every 8 iterations with 3-slice
+        # density-change builds in between (incremental Fock); "_full" keeps full 5-slice builds
+        inc = 1 if split else 0
+        runs = [("split" if split else "fp64", prec, None, inc)]
         if args.learned > 0:
             learned, D0, t_guess = learned_guess(binding, clusters, h, args.learned)
-            runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess)))
+            runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess), inc))
+            if split:
+                runs.append(("split_learned_full", prec, (D0, t_guess), 0))
         if split and args.compare_ttc:
-            runs.append(("fp64", binding.DF_PREC_FP64, None))
-        for label, p, g in runs:
-            res = h.scf(precision=p, slices=3, guess=None if g is None else g[0])
+            runs.append(("fp64", binding.DF_PREC_FP64, None, 0))
+        for label, p, g, inc in runs:
+            res = h.scf(precision=p, slices=3, incremental=inc, guess=None if g is None else g[0])
             ttc[label] = t_build + res["t_total_s"] + (0.0 if g is None else g[1])
             scf_info[label] = {"energy": res["energy"], "iterations": res["iterations"],
                                "converged": bool(res["converged"]), "t_iter_s": res["t_iter_s"],
-                               "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"]}
+                               "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"],
+                               "incremental_builds": res["incremental_builds"]}
 
     batched = None
     if args.batch > 0:
@@ -350,19 +358,19 @@ def batched_measure(binding, clusters, count, torch, rank=0, dev=None):
     seq = []
     for s in systems:
         with binding.Handle(s) as h:
-            seq.append(h.scf(precision=prec, slices=3))
+            seq.append(h.scf(precision=prec, slices=3, incremental=1))
     torch.cuda.synchronize()
     t_seq = max_over_ranks(time.perf_counter() - t0, dev)
     free, _ = torch.cuda.mem_get_info()
     t0 = time.perf_counter()
-    res = binding.scf_waves(systems, int(0.5 * free), precision=prec, slices=3)
+    res = binding.scf_waves(systems, int(0.5 * free), precision=prec, slices=3, incremental=1)
     torch.cuda.synchronize()
     t_batch = max_over_ranks(time.perf_counter() - t0, dev)
     de = max(abs(a["energy"] - b["energy"]) for a, b in zip(seq, res))
     return {"molecules": count, "waters": sizes, "basis_functions": int(sum(s.nbf for s in systems)),
             "t_sequential_s": t_seq, "t_batched_s": t_batch, "speedup": t_seq / t_batch,
             "all_converged": bool(all(r["converged"] for r in res)), "max_abs_dE_batch_vs_single": de,
-            "precision": "split (3 slices early, 5 late)"}
+            "precision": "split (3 slices early; late: 5-slice reference + 3-slice incremental builds)"}
 
 
 def ctypes_ptr(v):

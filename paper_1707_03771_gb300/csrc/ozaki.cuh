@@ -1,20 +1,33 @@
-// Ozaki error-free splitting shared by the split-precision kernels: a value already scaled by its
-// row's (or column's) power of two, |x| < 1, is written as sum_s m_s 2^{-7(s+1)} with integers
-// m_1 in [-128, 128] and m_{s>1} in [-64, 64], each exact in BF16.
+// Ozaki error-free splitting shared by the split-precision kernels: a value v of a row (or column)
+// whose power of two is e (|v 2^-e| < 1) is written as sum_s d_s 2^{-7s} 2^e + r, |r| <= 2^{-7S-1} 2^e,
+// with integer digits d_1 in [-128, 128] and d_{s>1} in [-64, 63], each exact in BF16.
 #pragma once
 #include <cuda_bf16.h>
 
 namespace dfhf {
 
+// 2^e as a double, -1022 <= e <= 1023
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// v 2^e for any e the slices produce (two exact power-of-two factors keep each in the normal range)
+__device__ __forceinline__ double scale_pow2(double v, int e) {
+    const int a = e / 2;
+    return (v * pow2d(a)) * pow2d(e - a);
+}
+
+// The digits come from one integer: T = rint(v 2^{7S-e}) (|T| <= 2^{7S}) peeled into balanced base-128
+// digits from the least significant end (d_S..d_2 in [-64, 63], d_1 the remaining quotient). One FP64
+// multiply and one conversion per value; the rest is integer arithmetic.
 template <int S>
-__device__ __forceinline__ void split_fp64(double x, __nv_bfloat16* out, long long stride) {
+__device__ __forceinline__ void split_pow2(double v, int e, __nv_bfloat16* out, long long stride) {
+    long long T = __double2ll_rn(scale_pow2(v, 7 * S - e));
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const double t = x * 128.0;
-        const double m = rint(t);
-        x = t - m;
-        out[s * stride] = __float2bfloat16_rn((float)m);
+    for (int s = S - 1; s >= 1; --s) {
+        const int d = (int)((T + 64) & 127) - 64;
+        out[s * stride] = __int2bfloat16_rn(d);
+        T = (T - d) >> 7;
     }
+    out[0] = __int2bfloat16_rn((int)T);
 }
 
 }  // namespace dfhf

@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(256) split_b_kernel(const double* __restrict__
     if (threadIdx.x == 0) Be[P * np + mu] = e;
     bf16* out = Bs + (P * np + mu) * (long long)np;
     for (int nu = threadIdx.x; nu < np; nu += blockDim.x) {
-        const double x = (mu < n && nu < n) ? ldexp(Bp[packed_index(mu, nu)], -e) : 0.0;
-        split_fp64<S>(x, out + nu, sstride);
+        const double x = (mu < n && nu < n) ? Bp[packed_index(mu, nu)] : 0.0;
+        split_pow2<S>(x, e, out + nu, sstride);
     }
 }
 
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(256) split_c_kernel(const double* __restrict__
     if (mx > 0.0) frexp(mx, &e);
     if (threadIdx.x == 0) Ce[i] = e;
     for (int nu = threadIdx.x; nu < np; nu += blockDim.x) {
-        const double x = (i < nocc && nu < n) ? ldexp(C[(long long)nu * nocc + i], -e) : 0.0;
-        split_fp64<S>(x, Cs + (long long)i * np + nu, sstride);
+        const double x = (i < nocc && nu < n) ? C[(long long)nu * nocc + i] : 0.0;
+        split_pow2<S>(x, e, Cs + (long long)i * np + nu, sstride);
     }
 }
 

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace dfhf {
 
@@ -374,7 +375,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 const int er = args.row_e[grow];
                 double* o = args.outd + (long long)grow * args.ldo + n0;
 #pragma unroll
-                for (int c = 0; c < N; ++c) o[c] = ldexp((double)hi[c] + (double)lo[c], er + __ldg(args.col_e + n0 + c));
+                for (int c = 0; c < N; ++c)
+                    o[c] = scale_pow2((double)hi[c] + (double)lo[c], er + __ldg(args.col_e + n0 + c));
             } else if (MODE == 0) {
                 const int er = args.row_e[(long long)P * args.np + grow];
                 float2* o = args.out + ((long long)P * args.np + grow) * args.ldy + n0;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     if (mx > 0.0) frexp(mx, &e);   // |row| * 2^-e < 1
     if (threadIdx.x == 0) eL[P] = e;
     bf16* o = Ls + (long long)P * kp;
-    for (int q = threadIdx.x; q < kp; q += blockDim.x) split_fp64<WS>(q < naux ? ldexp(row[q], -e) : 0.0, o + q, sstr);
+    for (int q = threadIdx.x; q < kp; q += blockDim.x) split_pow2<WS>(q < naux ? row[q] : 0.0, e, o + q, sstr);
 }
 
 // eA[c] = exponent of max_Q |A[Q][c0 + c]| for the chunk's columns
@@ -85,8 +85,7 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
     __syncthreads();
     for (int r = ty; r < 64; r += 4) {   // r: column within the tile, tx: Q within the tile
         const int c = cb + r;
-        const double x = ldexp(tile[tx][r], -eA[c]);
-        split_fp64<WS>(x, At + (long long)c * kp + q0 + tx, sstr);
+        split_pow2<WS>(tile[tx][r], eA[c], At + (long long)c * kp + q0 + tx, sstr);
     }
 }
 
