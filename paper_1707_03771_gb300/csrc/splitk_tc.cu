@@ -5,10 +5,11 @@
 //   * one CTA owns an output tile of 128 rows x N columns; every Ozaki level L = s + t (0-based) has
 //     its own FP32 accumulator of N columns in TMEM (S levels, S * N <= 512 columns);
 //   * a producer thread streams K-steps of 64 elements with TMA (3-D tensor maps, 128-byte swizzle):
-//     one step = slice s of the A tile (128 x 64) and the B slices t < S - s (N x 64 each), into a ring of
-//     shared-memory slots guarded by mbarriers;
-//   * one thread issues the MMAs (4 k16 instructions per step and B slice) and commits each slot back
-//     to the producer; at every chunk boundary it commits to the epilogue and waits until TMEM is free;
+//     the S B slices of a K-step (N x 64 each) once into one of two resident buffers, and the S A
+//     slices (128 x 64) through a ring of slots; every buffer is guarded by mbarriers;
+//   * one thread issues the MMAs: for A slice s, the B slices t < S - s in wide MMAs (4 k16 steps
+//     each), then commits the A slot back to the producer, and the B buffer after the K-step's last
+//     A slice; at every chunk boundary it commits to the epilogue and waits until TMEM is free;
 //   * four epilogue warps (one per 32 TMEM lanes) read the level sums with tcgen05.ld, scale them by the
 //     exact power of two 2^{e_row + e_col - 7 (L + 2)} and add them into per-thread float-float rows.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records DF_E_TIMEOUT in a flag,
@@ -38,7 +39,7 @@ constexpr int TM = 128;            // output rows per CTA (TMEM lanes)
 constexpr int KS = 64;             // K elements per pipeline step (one 128-byte swizzle row)
 constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks (S <= 5)
 constexpr int CHUNK_STEPS_W = 7;   // 448-element exact chunks (whitening, S = 7)
-constexpr int NSLOT = 3;
+constexpr int NA = 4;              // A-slice ring (one 128 x 64 slice per slot)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------------------------------------
@@ -161,8 +162,8 @@ template <int S, int N, int MODE>
 __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, TcArgs args) {
     constexpr int A_BYTES = TM * KS * 2;          // 16 KB
-    constexpr int B_BYTES = N * KS * 2;
-    constexpr int SLOT = ((A_BYTES + S * B_BYTES) + 1023) / 1024 * 1024;
+    constexpr int B_BYTES = N * KS * 2;           // a multiple of 1024 (N a multiple of 16)
+    constexpr int BSET = S * B_BYTES;             // every B slice of one K-step
     constexpr int NCOLS = S * N <= 32 ? 32 : (S * N <= 64 ? 64 : (S * N <= 128 ? 128 : (S * N <= 256 ? 256 : 512)));
     static_assert(S * N <= 512, "TMEM holds at most 512 accumulator columns");
     constexpr int MMA_SLICES = 256 / N;            // B slices per MMA (M = 128 allows N <= 256)
@@ -170,9 +171,12 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + NSLOT * SLOT);
-    uint64_t* empty = full + NSLOT;
-    uint64_t* acc_full = empty + NSLOT;
+    unsigned char* bbuf = smem + NA * A_BYTES;    // two B sets
+    uint64_t* a_full = (uint64_t*)(bbuf + 2 * BSET);
+    uint64_t* a_empty = a_full + NA;
+    uint64_t* b_full = a_empty + NA;
+    uint64_t* b_empty = b_full + 2;
+    uint64_t* acc_full = b_empty + 2;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* mma_done = acc_empty + 1;
     unsigned* tmem_slot = (unsigned*)(mma_done + 1);
@@ -183,7 +187,6 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     // ---- work decode -------------------------------------------------------------------------
     int P = 0, m0 = 0, n0 = 0, split = 0;
     int2 IJ = make_int2(0, 0);
-    int nsteps = 0;          // pipeline steps = K-steps x S
     int ksteps = 0;
     int p0 = 0, p1 = 0, kpp = 0;
     if (MODE == 0) {
@@ -217,13 +220,16 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         kpp = (args.ldy + KS - 1) / KS;
         ksteps = (p1 - p0) * kpp;
     }
-    nsteps = ksteps * S;
 
     // ---- set-up: barriers (thread 0), tensor memory (warp 0) ------------------------------------
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&b_full[i], 1);
+            mbar_init(&b_empty[i], 1);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -251,74 +257,94 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapA) : "memory");
             asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapB) : "memory");
-            int issued = 0;
-            for (int it = 0; it < nsteps; ++it) {
-                const int slot = it % NSLOT;
-                if (!mbar_wait(&empty[slot], ((it / NSLOT) & 1) ^ 1, err)) break;
-                const int ks = it / S, s = it % S;
-                const int nb = S - s;
-                mbar_expect_tx(&full[slot], A_BYTES + nb * B_BYTES);
-                unsigned char* base = smem + slot * SLOT;
-                if (MODE == 0) {
-                    const int kx = ks * KS;
-                    tma_load_3d(base, &mapA, kx, m0, s * args.naux + P, &full[slot]);
-                    for (int t = 0; t < nb; ++t) tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t, &full[slot]);
-                } else if (MODE == 2) {
-                    const int kx = ks * KS;
-                    tma_load_3d(base, &mapA, kx, m0, s, &full[slot]);
-                    for (int t = 0; t < nb; ++t) tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t, &full[slot]);
-                } else {
-                    const int Pr = p0 + ks / kpp, kx = (ks % kpp) * KS;
-                    tma_load_3d(base, &mapA, kx, m0, s * args.naux + Pr, &full[slot]);
-                    for (int t = 0; t < nb; ++t)
-                        tma_load_3d(base + A_BYTES + t * B_BYTES, &mapB, kx, n0, t * args.naux + Pr, &full[slot]);
+            int a_issued = 0, b_issued = 0;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                // tensor coordinates of this K-step: x (contraction), the auxiliary row for MODE 1
+                const int kx = MODE == 1 ? (ks % kpp) * KS : ks * KS;
+                const int Pr = MODE == 1 ? p0 + ks / kpp : 0;
+                const int bs = ks & 1;
+                if (!mbar_wait(&b_empty[bs], ((ks >> 1) & 1) ^ 1, err)) break;
+                mbar_expect_tx(&b_full[bs], BSET);
+                for (int t = 0; t < S; ++t) {
+                    const int zb = MODE == 1 ? t * args.naux + Pr : t;
+                    tma_load_3d(bbuf + bs * BSET + t * B_BYTES, &mapB, kx, n0, zb, &b_full[bs]);
                 }
-                ++issued;
+                ++b_issued;
+                bool ok = true;
+                for (int s = 0; s < S; ++s) {
+                    const int it = ks * S + s, slot = it % NA;
+                    if (!mbar_wait(&a_empty[slot], ((it / NA) & 1) ^ 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&a_full[slot], A_BYTES);
+                    const int za = MODE == 0 ? s * args.naux + P : (MODE == 2 ? s : s * args.naux + Pr);
+                    tma_load_3d(smem + slot * A_BYTES, &mapA, kx, m0, za, &a_full[slot]);
+                    ++a_issued;
+                }
+                if (!ok) break;
             }
-            // copies in flight complete before the kernel may leave: wait (bounded) for the last slots
-            if (*(volatile int*)err)
-                for (int it = max(0, issued - NSLOT); it < issued; ++it) {
+            // copies in flight complete before the kernel may leave: wait (bounded) for the last ones
+            if (*(volatile int*)err) {
+                for (int it = max(0, a_issued - NA); it < a_issued; ++it) {
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(&full[it % NSLOT], (it / NSLOT) & 1) && clock64() - t0 < WAIT_CYCLES) {
+                    while (!mbar_try_wait(&a_full[it % NA], (it / NA) & 1) && clock64() - t0 < WAIT_CYCLES) {
                     }
                 }
+                for (int k = max(0, b_issued - 2); k < b_issued; ++k) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&b_full[k & 1], (k >> 1) & 1) && clock64() - t0 < WAIT_CYCLES) {
+                    }
+                }
+            }
         }
     } else if (warp == 5) {
         // ---------------------------------- MMA issuer ----------------------------------------
         if (lane == 0) {
             int chunk = 0;
             bool ok = true;
-            for (int it = 0; it < nsteps && ok; ++it) {
-                const int ks = it / S, s = it % S;
+            for (int ks = 0; ks < ksteps && ok; ++ks) {
                 const int c = chunk_of(ks);
-                if (s == 0 && c != chunk) {       // new chunk: hand the finished sums to the epilogue
+                if (c != chunk) {                 // new chunk: hand the finished sums to the epilogue
                     mma_commit(acc_full);
                     ok = mbar_wait(acc_empty, (chunk & 1), err);
                     fence_after();
                     chunk = c;
                     if (!ok) break;
                 }
-                const int slot = it % NSLOT;
-                if (!mbar_wait(&full[slot], (it / NSLOT) & 1, err)) break;
-                fence_after();
-                unsigned char* base = smem + slot * SLOT;
-                const bool first_in_chunk = (s == 0) && (ks == 0 || chunk_of(ks - 1) != c);
-                // the B slices t < S - s are consecutive N-row tiles in shared memory and their levels
-                // s + t consecutive N-column accumulators in TMEM, so up to 256 / N of them form one MMA
-                // of width cnt * N (one read of the A tile per MMA instead of one per slice)
-#pragma unroll
-                for (int k = 0; k < KS / 16; ++k) {
-                    const uint64_t ad = smem_desc(base) + (uint64_t)(k * 2);   // +32 bytes per k16
-                    for (int t = 0; t < S - s; t += MMA_SLICES) {
-                        const int cnt = min(MMA_SLICES, S - s - t);
-                        const uint64_t bd = smem_desc(base + A_BYTES + t * B_BYTES) + (uint64_t)(k * 2);
-                        mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, instr_desc(TM, cnt * N),
-                                 (first_in_chunk && k == 0) ? 0u : 1u);
-                    }
+                const int bs = ks & 1;
+                if (!mbar_wait(&b_full[bs], (ks >> 1) & 1, err)) {
+                    ok = false;
+                    break;
                 }
-                mma_commit(&empty[slot]);
+                fence_after();
+                const bool first_in_chunk = ks == 0 || chunk_of(ks - 1) != c;
+                unsigned char* bset = bbuf + bs * BSET;
+                for (int s = 0; s < S; ++s) {
+                    const int it = ks * S + s, slot = it % NA;
+                    if (!mbar_wait(&a_full[slot], (it / NA) & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    // the B slices t < S - s are consecutive N-row tiles in shared memory and their levels
+                    // s + t consecutive N-column accumulators in TMEM, so up to 256 / N of them form one
+                    // MMA of width cnt * N (one read of the A tile per MMA instead of one per slice)
+#pragma unroll
+                    for (int k = 0; k < KS / 16; ++k) {
+                        const uint64_t ad = smem_desc(smem + slot * A_BYTES) + (uint64_t)(k * 2);   // +32 B per k16
+                        for (int t = 0; t < S - s; t += MMA_SLICES) {
+                            const int cnt = min(MMA_SLICES, S - s - t);
+                            const uint64_t bd = smem_desc(bset + t * B_BYTES) + (uint64_t)(k * 2);
+                            mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, instr_desc(TM, cnt * N),
+                                     (first_in_chunk && s == 0 && k == 0) ? 0u : 1u);
+                        }
+                    }
+                    mma_commit(&a_empty[slot]);
+                }
+                if (ok) mma_commit(&b_empty[bs]);
             }
-            if (ok && nsteps > 0) mma_commit(acc_full);
+            if (ok && ksteps > 0) mma_commit(acc_full);
             // every MMA this thread issued has completed before tensor memory is released
             mma_commit(mma_done);
             const long long t0 = clock64();
@@ -401,8 +427,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
 
 template <int S, int N>
 size_t tc_smem_bytes() {
-    constexpr int SLOT = ((TM * KS * 2 + S * N * KS * 2) + 1023) / 1024 * 1024;
-    return (size_t)NSLOT * SLOT + 1024 + 256;
+    return (size_t)NA * TM * KS * 2 + 2 * (size_t)S * N * KS * 2 + 1024 + 256;
 }
 
 // ------------------------------------------------------------------------------------------------
