@@ -274,6 +274,9 @@ def gpu_arm(args):
                     "y_split_tflops": y_tf, "k_split_tflops": k_tf,
                     "fp64_equivalent_tflops": alg_k_flops / ((avg["split_y_ms"] + avg["split_k_ms"] + avg["split_other_ms"]) * 1e-3) / 1e12}
     kernel_ms = {k: round(v, 3) for k, v in avg.items()}
+    tuned = per[-1]
+    autotune = {"y_tile_n": int(tuned.get("tc_y_tile_n", 0)), "k_split": int(tuned.get("tc_k_split", 0)),
+                "tuning_ms_this_process": round(float(tuned.get("autotune_ms", 0.0)), 1)} if split else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -295,6 +298,7 @@ def gpu_arm(args):
         "gpu_launches": args.steps * launches_per_step(prec),
         "roofline": roofline,
         "kernel_ms": kernel_ms,
+        "autotune": autotune,
         "compare": compare,
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],

@@ -221,7 +221,9 @@ int df_set_stream(df_handle* h, void* stream);
 /* Per-phase device times of the last df_build_B / df_jk in milliseconds (CUDA events):
  * [0] 1e+metric, [1] three-centre ERI, [2] Cholesky+inverse, [3] whitening, [4] gamma, [5] J,
  * [6] Y half-transform (FP64), [7] K contraction (FP64), [8] whole split exchange, [9] split Y,
- * [10] split K contraction, [11] split slicing and reduction. Up to `count` (<= 16) values are written. */
+ * [10] split K contraction, [11] split slicing and reduction, [12] tile width of the tensor-core Y
+ * kernel and [13] its K split chosen by the autotuner, [14] time the process has spent autotuning.
+ * Up to `count` (<= 16) values are written. */
 int df_timings(const df_handle* h, double* ms, int count);
 
 void df_free(df_handle* h);

@@ -145,6 +145,8 @@ struct df_handle {
     double timings_ms[16] = {0};
     std::vector<double> history;   // per SCF iteration: iteration, energy, dE, max|e|, slices, J/K ms
     bool sync_timing = true;       // per-kernel event timings (the batch driver turns them off)
+    int* tc_err_host = nullptr;    // set by the SCF driver: the tensor-core kernels' timeout flag is copied
+                                   // here (pinned) instead of being read back with a synchronisation
 };
 
 namespace dfhf {
@@ -173,6 +175,7 @@ void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* 
 
 // split precision (split_k.cu)
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK);
+void split_clear_error(df_handle* h);
 void free_split(df_handle* h);
 
 // SCF (scf.cu)

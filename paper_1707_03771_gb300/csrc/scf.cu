@@ -253,7 +253,10 @@ class ScfRun {
         slices_ = o_.slices;
         DF_CUDA(cudaMalloc((void**)&info_, sizeof(int)));
         DF_CUDA(cudaHostAlloc((void**)&pin_, sizeof(double) * 8, cudaHostAllocDefault));
-        DF_CUDA(cudaHostAlloc((void**)&pin_ctl_, sizeof(int) * (2 * DIIS_MAX + 2), cudaHostAllocDefault));
+        DF_CUDA(cudaHostAlloc((void**)&pin_ctl_, sizeof(int) * (2 * DIIS_MAX + 3), cudaHostAllocDefault));
+        pin_ctl_[2 * DIIS_MAX + 2] = 0;
+        h_->tc_err_host = pin_ctl_ + 2 * DIIS_MAX + 2;   // timeout flag of the tensor-core kernels
+        split_clear_error(h_);
         DF_CUDA(cudaEventCreate(&ev_done_));
         DF_CUDA(cudaEventCreate(&ej0_));
         DF_CUDA(cudaEventCreate(&ej1_));
@@ -359,6 +362,8 @@ class ScfRun {
         jk_ms_ += this_jk;
         if (pin_ctl_[2 * DIIS_MAX + 1] != 0)
             throw Error{DF_E_NUMERIC, "dsyevd failed, info " + std::to_string(pin_ctl_[2 * DIIS_MAX + 1])};
+        if (pin_ctl_[2 * DIIS_MAX + 2] != 0)
+            throw Error{DF_E_TIMEOUT, "tensor-core exchange kernel timed out waiting on a barrier"};
         if (pin_ctl_[2 * DIIS_MAX] != 0 && !order_.empty()) {   // last DIIS system was singular
             const int old = order_.front();
             if (old != slot_) {
@@ -533,6 +538,7 @@ class ScfRun {
     }
 
     void finish() {
+        h_->tc_err_host = nullptr;
         // all orbitals of the last Roothaan step, C = X V
         if (vt_ == Fp_) dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
         done_ = true;
@@ -544,6 +550,7 @@ class ScfRun {
     }
 
     void release() {
+        if (h_ && pin_ctl_ && h_->tc_err_host == pin_ctl_ + 2 * DIIS_MAX + 2) h_->tc_err_host = nullptr;
         if (work_) cudaFree(work_);
         if (info_) cudaFree(info_);
         if (d_ints_) cudaFree(d_ints_);

@@ -17,6 +17,11 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <vector>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -426,8 +431,8 @@ bool use_tensor_cores() {
 
 }  // namespace
 
-void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux, int np,
-                int ldy, float2* Y, int* err);
+void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux,
+                int np, int ldy, float2* Y, int* err);
 void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
                 const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
 void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K);
@@ -437,7 +442,8 @@ struct SplitState {
     int* err = nullptr;          // device error word of the tcgen05 kernels
     int2* tiles128 = nullptr;    // lower 128-tile pairs
     float2* Kpart_tc = nullptr;  // [nsplit_tc][npt][npt]
-    int npt = 0, ntiles128 = 0, nsplit_tc = 0;
+    int npt = 0, ntiles128 = 0, nsplit_tc = 0, kcap = 0;   // kcap: splits Kpart_tc has room for
+    int yN = 80;                 // tile width of the tensor-core Y kernel
     int S = 0;
     int np = 0;
     bf16* Bs = nullptr;
@@ -484,6 +490,81 @@ void prepare_b(df_handle* h, SplitState* st) {
     DF_CHECK_LAUNCH();
 }
 
+// ---- autotuner ----------------------------------------------------------------------------------
+// The tile width N of the tensor-core Y kernel (32, 64 or 80 columns dividing ldy) and the split of the
+// K kernel over auxiliary blocks are picked by timing the candidates on the call's own operands the
+// first time a size bucket (np, ldy, naux / 512, S) is met; the choice is kept for the process.
+struct TcChoice {
+    int yN = 0, ksplit = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, TcChoice> g_tune;
+double g_tune_ms = 0.0;
+
+template <typename F>
+double time_once(cudaStream_t s, F&& launch) {
+    cudaEvent_t a, b;
+    DF_CUDA(cudaEventCreate(&a));
+    DF_CUDA(cudaEventCreate(&b));
+    launch();   // warm-up: first-launch attribute and module set-up
+    DF_CUDA(cudaEventRecord(a, s));
+    launch();
+    DF_CUDA(cudaEventRecord(b, s));
+    DF_CUDA(cudaEventSynchronize(b));
+    const double ms = elapsed_ms(a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+template <int S>
+TcChoice autotune_tc(df_handle* h, SplitState* st) {
+    cudaStream_t s = h->stream;
+    const int np = st->np, ldy = st->ldy, naux = h->naux;
+    const auto t0 = std::chrono::steady_clock::now();
+    TcChoice best;
+    double best_ms = 1e30;
+    for (int N : {80, 64, 32}) {
+        if (ldy % N) continue;
+        const double ms = time_once(s, [&] { y_split_tc(s, S, N, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err); });
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.yN = N;
+        }
+    }
+    const long long nblk = (naux + st->PB - 1) / st->PB;
+    const long long ystr = (long long)naux * np * ldy;
+    split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
+    DF_CHECK_LAUNCH();
+    const int h0 = st->nsplit_tc;   // the occupancy heuristic: about 4 CTAs per SM
+    std::vector<int> cands;
+    for (int c : {1, std::max(1, h0 / 2), h0, 2 * h0, 4 * h0}) {
+        const long long bytes = (long long)c * st->npt * st->npt * sizeof(float2);
+        if (c >= 1 && c <= nblk && bytes <= (2LL << 30) && std::find(cands.begin(), cands.end(), c) == cands.end())
+            cands.push_back(c);
+    }
+    const int cmax = *std::max_element(cands.begin(), cands.end());
+    if (cmax > st->kcap) {
+        cudaFree(st->Kpart_tc);
+        st->Kpart_tc = nullptr;
+        DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * cmax * (long long)st->npt * st->npt));
+        st->kcap = cmax;
+    }
+    best_ms = 1e30;
+    for (int c : cands) {
+        const double ms = time_once(s, [&] {
+            k_split_tc(s, S, st->Ys, st->Ye, naux, np, ldy, st->PB, c, st->tiles128, st->ntiles128, st->Kpart_tc,
+                       st->npt, st->err);
+        });
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.ksplit = c;
+        }
+    }
+    g_tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return best;
+}
+
 template <int S>
 void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK, cudaEvent_t* ev) {
     cudaStream_t s = h->stream;
@@ -499,9 +580,41 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 gy(np / 64, naux, (ldy + BN - 1) / BN);
     const bool tc = use_tensor_cores() && (S == 3 || S == 5);
+    if (tc) {
+        const std::array<int, 4> key{np, ldy, (naux + 511) / 512, S};
+        TcChoice ch;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                ch = it->second;
+                have = true;
+            }
+        }
+        if (!have) {
+            ch = autotune_tc<S>(h, st);
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[key] = ch;
+        }
+        st->yN = ch.yN;
+        // a choice made for another handle of the bucket: at most one split per auxiliary block, and
+        // room for it in the partial-sum buffer
+        const int ksplit = (int)std::min<long long>(ch.ksplit, (naux + st->PB - 1) / st->PB);
+        if (ksplit > st->kcap) {
+            cudaFree(st->Kpart_tc);
+            st->Kpart_tc = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * ksplit * (long long)st->npt * st->npt));
+            st->kcap = ksplit;
+        }
+        st->nsplit_tc = ksplit;
+        h->timings_ms[12] = ch.yN;
+        h->timings_ms[13] = st->nsplit_tc;
+        h->timings_ms[14] = g_tune_ms;
+    }
     DF_CUDA(cudaEventRecord(ev[0], s));
     if (tc) {
-        y_split_tc(s, S, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err);
+        y_split_tc(s, S, st->yN, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err);
     } else {
         y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np,
                                                      ldy, st->Y);
@@ -592,7 +705,10 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * nblk * np));
         DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
         // tcgen05 K: lower 128-tile pairs, split over auxiliary blocks to fill the GPU
-        if (!st->err) DF_CUDA(cudaMalloc((void**)&st->err, sizeof(int)));
+        if (!st->err) {
+            DF_CUDA(cudaMalloc((void**)&st->err, sizeof(int)));
+            DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
+        }
         const int nt128 = (int)((np + 127) / 128);
         st->npt = nt128 * 128;
         st->ntiles128 = nt128 * (nt128 + 1) / 2;
@@ -607,8 +723,11 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         cudaFree(st->Kpart_tc);
         st->Kpart_tc = nullptr;
         DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * st->nsplit_tc * (long long)st->npt * st->npt));
+        st->kcap = st->nsplit_tc;
     }
-    if (st->err) DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
+    // synchronous callers clear the timeout flag per call; under the SCF driver it stays set once
+    // raised and is read with the iteration's scalars
+    if (st->err && !h->tc_err_host) DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
     switch (slices) {
         case 2: run_split<2>(h, st, dC, nocc, dK, ev); break;
         case 3: run_split<3>(h, st, dC, nocc, dK, ev); break;
@@ -616,7 +735,9 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         default: run_split<5>(h, st, dC, nocc, dK, ev); break;
     }
     DF_CUDA(cudaEventRecord(e1, h->stream));
-    if (st->err) {
+    if (st->err && h->tc_err_host) {
+        DF_CUDA(cudaMemcpyAsync(h->tc_err_host, st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    } else if (st->err) {
         // the tcgen05 kernels bound their waits and report expiry here
         int herr = 0;
         DF_CUDA(cudaMemcpyAsync(&herr, st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -633,6 +754,10 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (auto& e : ev) cudaEventDestroy(e);
+}
+
+void split_clear_error(df_handle* h) {
+    if (h->split && h->split->err) DF_CUDA(cudaMemsetAsync(h->split->err, 0, sizeof(int), h->stream));
 }
 
 }  // namespace dfhf

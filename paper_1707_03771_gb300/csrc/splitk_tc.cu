@@ -500,11 +500,18 @@ void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n
     DF_CHECK_LAUNCH();
 }
 
-// Y[P][mu][i] (float pairs) = B_P C from the slices Bs [S][naux][np][np], Cs [S][ldy][np]
-void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux, int np,
-                int ldy, float2* Y, int* err) {
-    constexpr int N = 80;
-    if (ldy % 32) throw Error{DF_E_ARG, "tensor-core split Y: occupied width must be a multiple of 32"};
+// Y[P][mu][i] (float pairs) = B_P C from the slices Bs [S][naux][np][np], Cs [S][ldy][np]; CTA tiles
+// of 128 rows x N columns, N in {32, 64, 80} dividing ldy (chosen by the autotuner)
+template <int S, int N>
+void y_tc_launch(cudaStream_t s, const CUtensorMap& ma, const bf16* Cs, int np, int ldy, const TcArgs& a, int naux) {
+    const CUtensorMap mb = make_map(Cs, np, ldy, S, N);
+    const unsigned mt = (np + TM - 1) / TM;
+    launch_tc<S, N, 0>(s, ma, mb, a, (unsigned)naux * mt * (ldy / N));
+}
+
+void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux,
+                int np, int ldy, float2* Y, int* err) {
+    if (ldy % N) throw Error{DF_E_ARG, "tensor-core split Y: tile width must divide the occupied width"};
     TcArgs a{};
     a.mode = 0;
     a.naux = naux;
@@ -515,25 +522,13 @@ void y_split_tc(cudaStream_t s, int S, const bf16* Bs, const int* Be, const bf16
     a.out = Y;
     a.err = err;
     const CUtensorMap ma = make_map(Bs, np, np, (unsigned long long)S * naux, TM);
-    const unsigned mt = (np + TM - 1) / TM;
-    if (ldy % N == 0) {
-        const CUtensorMap mb = make_map(Cs, np, ldy, S, N);
-        const unsigned grid = (unsigned)naux * mt * (ldy / N);
-        switch (S) {
-            case 3: launch_tc<3, N, 0>(s, ma, mb, a, grid); break;
-            case 5: launch_tc<5, N, 0>(s, ma, mb, a, grid); break;
-            default: throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices"};
-        }
-    } else {
-        constexpr int N2 = 32;
-        const CUtensorMap mb = make_map(Cs, np, ldy, S, N2);
-        const unsigned grid = (unsigned)naux * mt * (ldy / N2);
-        switch (S) {
-            case 3: launch_tc<3, N2, 0>(s, ma, mb, a, grid); break;
-            case 5: launch_tc<5, N2, 0>(s, ma, mb, a, grid); break;
-            default: throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices"};
-        }
-    }
+    if (S == 3 && N == 80) y_tc_launch<3, 80>(s, ma, Cs, np, ldy, a, naux);
+    else if (S == 5 && N == 80) y_tc_launch<5, 80>(s, ma, Cs, np, ldy, a, naux);
+    else if (S == 3 && N == 64) y_tc_launch<3, 64>(s, ma, Cs, np, ldy, a, naux);
+    else if (S == 5 && N == 64) y_tc_launch<5, 64>(s, ma, Cs, np, ldy, a, naux);
+    else if (S == 3 && N == 32) y_tc_launch<3, 32>(s, ma, Cs, np, ldy, a, naux);
+    else if (S == 5 && N == 32) y_tc_launch<5, 32>(s, ma, Cs, np, ldy, a, naux);
+    else throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices and tile widths 32, 64, 80"};
 }
 
 // B[P][c] = sum_Q L^-1[P][Q] A[Q][c] for the ncols columns of one chunk, from the 7 slices

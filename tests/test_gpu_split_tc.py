@@ -47,3 +47,27 @@ def test_tensor_core_split_matches_mma_sync_and_fp64(lib, name, slices):
     assert np.array_equal(Ktc, Ktc2)
     assert np.abs(Ktc - Kms).max() <= 1e-12 * scale, np.abs(Ktc - Kms).max() / scale
     assert np.abs(Ktc - K64).max() <= 2.0 ** (7 - 7 * slices) * scale
+
+
+def test_autotuner_choice_is_valid_and_cached(lib):
+    """The autotuner picks a Y tile width dividing the occupied width and a K split of at least one
+    auxiliary block; a second molecule of the same size bucket reuses the choice without tuning."""
+    system = clusters.workload("water8")
+    rng = np.random.default_rng(4)
+    with lib.Handle(system) as h:
+        h.build_B()
+        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+        D = 2 * C @ C.T
+        K1 = _k(h, lib, D, C, 5, tc=True)
+        t1 = h.timings()
+    ldy = (system.nocc + 31) // 32 * 32
+    assert t1["tc_y_tile_n"] in (32, 64, 80) and ldy % int(t1["tc_y_tile_n"]) == 0
+    assert t1["tc_k_split"] >= 1
+    assert t1["autotune_ms"] > 0
+    with lib.Handle(system) as h:
+        h.build_B()
+        K2 = _k(h, lib, D, C, 5, tc=True)
+        t2 = h.timings()
+    assert t2["autotune_ms"] == t1["autotune_ms"]          # no new tuning for the same bucket
+    assert (t2["tc_y_tile_n"], t2["tc_k_split"]) == (t1["tc_y_tile_n"], t1["tc_k_split"])
+    assert np.array_equal(K1, K2)
