@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <vector>
+#include <cstdio>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -433,8 +434,8 @@ bool use_tensor_cores() {
 
 void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux,
                 int np, int ldy, float2* Y, int* err);
-void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
-                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
+void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB,
+                int nsplit, const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
 void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K);
 
 struct SplitState {
@@ -444,6 +445,7 @@ struct SplitState {
     float2* Kpart_tc = nullptr;  // [nsplit_tc][npt][npt]
     int npt = 0, ntiles128 = 0, nsplit_tc = 0, kcap = 0;   // kcap: splits Kpart_tc has room for
     int yN = 80;                 // tile width of the tensor-core Y kernel
+    int kN = 64;                 // half-tile width of the tensor-core K kernel
     int S = 0;
     int np = 0;
     bf16* Bs = nullptr;
@@ -495,7 +497,7 @@ void prepare_b(df_handle* h, SplitState* st) {
 // K kernel over auxiliary blocks are picked by timing the candidates on the call's own operands the
 // first time a size bucket (np, ldy, naux / 512, S) is met; the choice is kept for the process.
 struct TcChoice {
-    int yN = 0, ksplit = 0;
+    int yN = 0, kN = 64, ksplit = 0;
 };
 std::mutex g_tune_mu;
 std::map<std::array<int, 4>, TcChoice> g_tune;
@@ -550,11 +552,23 @@ TcChoice autotune_tc(df_handle* h, SplitState* st) {
         DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * cmax * (long long)st->npt * st->npt));
         st->kcap = cmax;
     }
+    // K: the half-tile width at the occupancy heuristic's split, then the split at that width
+    best_ms = 1e30;
+    for (int N : {64, 32}) {
+        const double ms = time_once(s, [&] {
+            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, h0 <= cmax ? h0 : cmax, st->tiles128,
+                       st->ntiles128, st->Kpart_tc, st->npt, st->err);
+        });
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.kN = N;
+        }
+    }
     best_ms = 1e30;
     for (int c : cands) {
         const double ms = time_once(s, [&] {
-            k_split_tc(s, S, st->Ys, st->Ye, naux, np, ldy, st->PB, c, st->tiles128, st->ntiles128, st->Kpart_tc,
-                       st->npt, st->err);
+            k_split_tc(s, S, best.kN, st->Ys, st->Ye, naux, np, ldy, st->PB, c, st->tiles128, st->ntiles128,
+                       st->Kpart_tc, st->npt, st->err);
         });
         if (ms < best_ms) {
             best_ms = ms;
@@ -592,12 +606,22 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
                 have = true;
             }
         }
+        // DFHF_TC_TILES="yN,kN,ksplit" fixes the choice (tests compare tilings; the results do not depend on it)
+        if (const char* f = std::getenv("DFHF_TC_TILES")) {
+            TcChoice fc;
+            if (std::sscanf(f, "%d,%d,%d", &fc.yN, &fc.kN, &fc.ksplit) == 3 && fc.ksplit >= 1 &&
+                (fc.yN == 32 || fc.yN == 64 || fc.yN == 80) && ldy % fc.yN == 0 && (fc.kN == 32 || fc.kN == 64)) {
+                ch = fc;
+                have = true;
+            }
+        }
         if (!have) {
             ch = autotune_tc<S>(h, st);
             std::lock_guard<std::mutex> lock(g_tune_mu);
             g_tune[key] = ch;
         }
         st->yN = ch.yN;
+        st->kN = ch.kN;
         // a choice made for another handle of the bucket: at most one split per auxiliary block, and
         // room for it in the partial-sum buffer
         const int ksplit = (int)std::min<long long>(ch.ksplit, (naux + st->PB - 1) / st->PB);
@@ -631,7 +655,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
     DF_CUDA(cudaEventRecord(ev[2], s));
     if (tc) {
-        k_split_tc(s, S, st->Ys, st->Ye, naux, np, ldy, st->PB, st->nsplit_tc, st->tiles128, st->ntiles128,
+        k_split_tc(s, S, st->kN, st->Ys, st->Ye, naux, np, ldy, st->PB, st->nsplit_tc, st->tiles128, st->ntiles128,
                    st->Kpart_tc, st->npt, st->err);
         DF_CUDA(cudaEventRecord(ev[3], s));
         k_tc_reduce(s, st->Kpart_tc, st->nsplit_tc, st->npt, h->n, dK);

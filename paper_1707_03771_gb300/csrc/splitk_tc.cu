@@ -39,7 +39,11 @@ constexpr int TM = 128;            // output rows per CTA (TMEM lanes)
 constexpr int KS = 64;             // K elements per pipeline step (one 128-byte swizzle row)
 constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks (S <= 5)
 constexpr int CHUNK_STEPS_W = 7;   // 448-element exact chunks (whitening, S = 7)
-constexpr int NA = 4;              // A-slice ring (one 128 x 64 slice per slot)
+// A-slice ring slots (one 128 x 64 slice each): 4, or 3 where that lets two CTAs share an SM
+template <int S, int N>
+constexpr int ring_slots() {
+    return (S >= 7 && N <= 32) ? 3 : 4;
+}
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------------------------------------
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     constexpr int A_BYTES = TM * KS * 2;          // 16 KB
     constexpr int B_BYTES = N * KS * 2;           // a multiple of 1024 (N a multiple of 16)
     constexpr int BSET = S * B_BYTES;             // every B slice of one K-step
+    constexpr int NA = ring_slots<S, N>();
     constexpr int NCOLS = S * N <= 32 ? 32 : (S * N <= 64 ? 64 : (S * N <= 128 ? 128 : (S * N <= 256 ? 256 : 512)));
     static_assert(S * N <= 512, "TMEM holds at most 512 accumulator columns");
     constexpr int MMA_SLICES = 256 / N;            // B slices per MMA (M = 128 allows N <= 256)
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
 
 template <int S, int N>
 size_t tc_smem_bytes() {
-    return (size_t)NA * TM * KS * 2 + 2 * (size_t)S * N * KS * 2 + 1024 + 256;
+    return (size_t)ring_slots<S, N>() * TM * KS * 2 + 2 * (size_t)S * N * KS * 2 + 1024 + 256;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -534,9 +539,10 @@ void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, con
 // B[P][c] = sum_Q L^-1[P][Q] A[Q][c] for the ncols columns of one chunk, from the 7 slices
 // Ls [7][naux][kp] (row exponents eL) and At [7][ncols][kp] (column exponents eA); rows of `out` have
 // stride ldo. kp is naux padded to a multiple of 64 (zero slices beyond naux), ncols a multiple of 64.
-void whiten_tc(cudaStream_t s, const bf16* Ls, const int* eL, const bf16* At, const int* eA, int naux, int kp,
-               int ncols, double* out, long long ldo, int* err) {
-    constexpr int S = 7, N = 64;
+template <int N>
+void whiten_tc_n(cudaStream_t s, const bf16* Ls, const int* eL, const bf16* At, const int* eA, int naux, int kp,
+                 int ncols, double* out, long long ldo, int* err) {
+    constexpr int S = 7;
     if (kp % KS || ncols % N) throw Error{DF_E_ARG, "internal: whitening operands not padded to 64"};
     TcArgs a{};
     a.mode = 2;
@@ -554,10 +560,18 @@ void whiten_tc(cudaStream_t s, const bf16* Ls, const int* eL, const bf16* At, co
     launch_tc<S, N, 2>(s, ma, mb, a, grid);
 }
 
+// N: output tile width, 64 or 32 (32: two CTAs per SM)
+void whiten_tc(cudaStream_t s, int N, const bf16* Ls, const int* eL, const bf16* At, const int* eA, int naux, int kp,
+               int ncols, double* out, long long ldo, int* err) {
+    if (N == 64) whiten_tc_n<64>(s, Ls, eL, At, eA, naux, kp, ncols, out, ldo, err);
+    else if (N == 32) whiten_tc_n<32>(s, Ls, eL, At, eA, naux, kp, ncols, out, ldo, err);
+    else throw Error{DF_E_ARG, "tensor-core whitening supports tile widths 32 and 64"};
+}
+
 // K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs)
-void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
-                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
-    constexpr int N = 64;
+template <int N>
+void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
+                  const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
     TcArgs a{};
     a.mode = 1;
     a.naux = naux;
@@ -578,6 +592,14 @@ void k_split_tc(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, 
         case 5: launch_tc<5, N, 1>(s, ma, mb, a, grid); break;
         default: throw Error{DF_E_ARG, "tensor-core split K supports 3 or 5 slices"};
     }
+}
+
+// N: width of the column half-tiles of each 128 x 128 output tile, 64 or 32
+void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB,
+                int nsplit, const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
+    if (N == 64) k_split_tc_n<64>(s, S, Ys, Ye, naux, np, ldy, PB, nsplit, tiles128, ntiles, Kpart, npt, err);
+    else if (N == 32) k_split_tc_n<32>(s, S, Ys, Ye, naux, np, ldy, PB, nsplit, tiles128, ntiles, Kpart, npt, err);
+    else throw Error{DF_E_ARG, "tensor-core split K supports tile widths 32 and 64"};
 }
 
 }  // namespace dfhf

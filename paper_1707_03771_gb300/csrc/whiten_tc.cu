@@ -14,19 +14,28 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "ozaki.cuh"
 
 namespace dfhf {
 
-void whiten_tc(cudaStream_t s, const __nv_bfloat16* Ls, const int* eL, const __nv_bfloat16* At, const int* eA,
+void whiten_tc(cudaStream_t s, int N, const __nv_bfloat16* Ls, const int* eL, const __nv_bfloat16* At, const int* eA,
                int naux, int kp, int ncols, double* out, long long ldo, int* err);
 
 namespace {
 
 typedef __nv_bfloat16 bf16;
 constexpr int WS = 7;   // slices
+
+// Output tile width of the whitening kernel (64, or 32 with two CTAs per SM), chosen per size bucket
+// (naux / 512) by timing the first two column chunks of the first whitening in that bucket with one
+// width each: the candidates run on real work, so the choice costs nothing extra.
+std::mutex g_wmu;
+std::map<int, int> g_wtile;
 
 // L^-1 (naux x naux, row-major, lower) -> Ls[s][P][Q] (kp columns, zero beyond naux), eL[P]
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ L, int naux, int kp,
@@ -114,14 +123,44 @@ void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const 
     err.zero(s);
     slice_rows_kernel<<<naux, 256, 0, s>>>(Linv, naux, kp, Ls.p, (long long)naux * kp, eL.p);
     DF_CHECK_LAUNCH();
-    for (long long c0 = 0; c0 < ncol; c0 += nc) {
+    const int bucket = (naux + 511) / 512;
+    int tile = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_wmu);
+        auto it = g_wtile.find(bucket);
+        if (it != g_wtile.end()) tile = it->second;
+    }
+    if (const char* f = std::getenv("DFHF_WHITEN_TILE")) {   // fixes the width (tests compare the two)
+        const int t = std::atoi(f);
+        if (t == 32 || t == 64) tile = t;
+    }
+    const bool tune = tile == 0 && ncol >= 2 * nc;   // two full-width chunks to compare
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (tune)
+        for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
+    int k = 0;
+    for (long long c0 = 0; c0 < ncol; c0 += nc, ++k) {
         const int w = (int)std::min<long long>(nc, ncol - c0);
         col_exponent_kernel<<<(w + 255) / 256, 256, 0, s>>>(A, ld, naux, c0, w, eA.p);
         DF_CHECK_LAUNCH();
         slice_cols_kernel<<<dim3(w / 64, kp / 64), 256, 0, s>>>(A, ld, naux, kp, c0, eA.p, At.p, (long long)w * kp);
         DF_CHECK_LAUNCH();
-        whiten_tc(s, Ls.p, eL.p, At.p, eA.p, naux, kp, w, B + c0, ld, err.p);
+        int use = tile ? tile : 64;
+        if (tune && k < 2) {
+            use = k == 0 ? 64 : 32;
+            DF_CUDA(cudaEventRecord(ev[2 * k], s));
+        }
+        whiten_tc(s, use, Ls.p, eL.p, At.p, eA.p, naux, kp, w, B + c0, ld, err.p);
+        if (tune && k < 2) DF_CUDA(cudaEventRecord(ev[2 * k + 1], s));
+        if (tune && k == 1) {
+            DF_CUDA(cudaEventSynchronize(ev[3]));
+            tile = elapsed_ms(ev[2], ev[3]) < elapsed_ms(ev[0], ev[1]) ? 32 : 64;
+            std::lock_guard<std::mutex> lock(g_wmu);
+            g_wtile[bucket] = tile;
+        }
     }
+    if (tune)
+        for (auto& e : ev) cudaEventDestroy(e);
     int herr = 0;
     DF_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     DF_CUDA(cudaStreamSynchronize(s));

@@ -71,3 +71,25 @@ def test_autotuner_choice_is_valid_and_cached(lib):
     assert t2["autotune_ms"] == t1["autotune_ms"]          # no new tuning for the same bucket
     assert (t2["tc_y_tile_n"], t2["tc_k_split"]) == (t1["tc_y_tile_n"], t1["tc_k_split"])
     assert np.array_equal(K1, K2)
+
+
+@pytest.mark.parametrize("slices", [3, 5])
+def test_tile_widths_give_identical_exchange(lib, slices):
+    """Every tile width and split of the tensor-core kernels performs the same per-element arithmetic
+    (same exact chunk sums, same drain order), so K is bitwise identical across tilings."""
+    system = clusters.workload("water8")
+    rng = np.random.default_rng(6)
+    out = {}
+    with lib.Handle(system) as h:
+        h.build_B()
+        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+        D = 2 * C @ C.T
+        for tiles in ("32,64,4", "64,32,4", "32,32,4"):
+            os.environ["DFHF_TC_TILES"] = tiles
+            try:
+                out[tiles] = _k(h, lib, D, C, slices, tc=True)
+            finally:
+                del os.environ["DFHF_TC_TILES"]
+    ref = out["32,64,4"]
+    for k, v in out.items():
+        assert np.array_equal(v, ref), k

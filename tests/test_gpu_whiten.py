@@ -74,3 +74,19 @@ def test_keep_and_in_place_agree(lib):
     finally:
         a.close()
         b.close()
+
+
+def test_whitening_tile_widths_identical(lib):
+    """The 64- and 32-column whitening tiles do the same per-element arithmetic: bitwise equal B."""
+    system = clusters.workload("water8")
+    out = []
+    for t in ("64", "32"):
+        os.environ["DFHF_WHITEN_TILE"] = t
+        try:
+            h = _build(lib, system, None, keep=False)
+            out.append(h.rows(1, 0, 3))
+            out.append(h.rows(1, system.naux - 2, 2))
+            h.close()
+        finally:
+            del os.environ["DFHF_WHITEN_TILE"]
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
