@@ -121,6 +121,11 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel and tile on the same workload;
+# keyed by (workload, kernel, slices, tile width). Anything not captured reports null.
+NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.57e9 + 8.97e9, ("water32", "K", 5, 32): 73.31e9 + 0.04e9}
+
 # FP64 DFMA peak of GB300 measured with a dependent-chain-free DFMA loop over all 152 SMs
 # (1.00 TFLOP/s; DMMA m8n8k4 gave 1.05 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.00
@@ -266,16 +271,23 @@ def gpu_arm(args):
         tc = os.environ.get("DFHF_SPLIT_TC", "1") != "0" and S in (3, 5)
         kname = ("ozaki_tc_kernel<Y>" if dom_y else "ozaki_tc_kernel<K>") + " (tcgen05 BF16, TMEM, TMA)" if tc else \
             ("y_split_kernel" if dom_y else "k_split_kernel") + " (BF16 mma.sync)"
+        tuned_tiles = per[-1]
+        tile = int(tuned_tiles.get("tc_y_tile_n" if dom_y else "tc_k_tile_n", 0))
+        traffic = NCU_TRAFFIC.get((args.workload, "Y" if dom_y else "K", S, tile)) if tc else None
         roofline = {"kernel": kname + ", Ozaki slices",
                     "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                     "frac": achieved / pk if pk else None,
                     "peak_source": f"{peak_src} bf16_tflops (cuBLAS burst)",
-                    "traffic": None,
+                    "traffic": traffic,
+                    "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                    "algorithmic_bytes": (S * naux * npad * npad * 2 + naux * npad * ldy * 8) if dom_y else
+                                         (S * naux * npad * ldy * 2),
                     "y_split_tflops": y_tf, "k_split_tflops": k_tf,
                     "fp64_equivalent_tflops": alg_k_flops / ((avg["split_y_ms"] + avg["split_k_ms"] + avg["split_other_ms"]) * 1e-3) / 1e12}
     kernel_ms = {k: round(v, 3) for k, v in avg.items()}
     tuned = per[-1]
-    autotune = {"y_tile_n": int(tuned.get("tc_y_tile_n", 0)), "k_split": int(tuned.get("tc_k_split", 0)),
+    autotune = {"y_tile_n": int(tuned.get("tc_y_tile_n", 0)), "k_tile_n": int(tuned.get("tc_k_tile_n", 0)),
+                "k_split": int(tuned.get("tc_k_split", 0)),
                 "tuning_ms_this_process": round(float(tuned.get("autotune_ms", 0.0)), 1)} if split else None
 
     cpu = None

@@ -222,7 +222,8 @@ int df_set_stream(df_handle* h, void* stream);
  * [0] 1e+metric, [1] three-centre ERI, [2] Cholesky+inverse, [3] whitening, [4] gamma, [5] J,
  * [6] Y half-transform (FP64), [7] K contraction (FP64), [8] whole split exchange, [9] split Y,
  * [10] split K contraction, [11] split slicing and reduction, [12] tile width of the tensor-core Y
- * kernel and [13] its K split chosen by the autotuner, [14] time the process has spent autotuning.
+ * kernel, [13] K split and [15] K tile width chosen by the autotuner, [14] time the process has spent
+ * autotuning.
  * Up to `count` (<= 16) values are written. */
 int df_timings(const df_handle* h, double* ms, int count);
 

@@ -635,6 +635,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         h->timings_ms[12] = ch.yN;
         h->timings_ms[13] = st->nsplit_tc;
         h->timings_ms[14] = g_tune_ms;
+        h->timings_ms[15] = st->kN;
     }
     DF_CUDA(cudaEventRecord(ev[0], s));
     if (tc) {
