@@ -55,13 +55,13 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
-def batch_members(count, rank):
+def batch_members(count, rank, wmax=8):
     """The clusters of one rank's batched-SCF measurement: `count` (waters, seed) pairs, sizes drawn
-    uniformly from 1-8 waters, seeds 1000 + rank * count + k, so replicas solve disjoint molecule sets of
-    the same size distribution (weak scaling: the work per GPU does not change with the rank count)."""
+    uniformly from 1-wmax waters, seeds 1000 + rank * count + k, so replicas solve disjoint molecule sets
+    of the same size distribution (weak scaling: the work per GPU does not change with the rank count)."""
     from paper_1707_03771_gb300 import clusters
     rng = clusters.SplitMix64(4242 + rank)
-    return [(1 + min(7, int(rng.uniform() * 8)), 1000 + rank * count + k) for k in range(count)]
+    return [(1 + min(wmax - 1, int(rng.uniform() * wmax)), 1000 + rank * count + k) for k in range(count)]
 
 
 class ClockSampler:
@@ -147,6 +147,9 @@ def gpu_arm(args):
         tdist.barrier()
     lib = binding.load()
     system = clusters.workload(args.workload)
+    guess_net = None
+    if args.ttc and args.learned > 0:
+        guess_net, learned = learned_guess_net(binding, clusters, args.learned)
     split = args.precision == "split"
     prec = binding.DF_PREC_SPLIT if split else binding.DF_PREC_FP64
     S = args.slices
@@ -218,30 +221,45 @@ def gpu_arm(args):
     # and from the learned guess (network trained beforehand on smaller clusters; training not timed)
     ttc = {}
     scf_info = {}
-    learned = None
+    if guess_net is None:
+        learned = None
     if args.ttc:
         # split precision: S = 3 early, then a 5-slice reference K every 8 iterations with 3-slice
         # density-change builds in between (incremental Fock); "_full" keeps full 5-slice builds
         inc = 1 if split else 0
         runs = [("split" if split else "fp64", prec, None, inc)]
-        if args.learned > 0:
-            learned, D0, t_guess = learned_guess(binding, clusters, h, args.learned)
+        if guess_net is not None:
+            t0 = time.perf_counter()
+            D0 = h.mlp_guess(guess_net, bf16=True)
+            t_guess = time.perf_counter() - t0
+            guess_net.close()
+            learned["t_guess_s"] = t_guess
             runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess), inc))
             if split:
                 runs.append(("split_learned_full", prec, (D0, t_guess), 0))
         if split and args.compare_ttc:
             runs.append(("fp64", binding.DF_PREC_FP64, None, 0))
+        hist = {}
         for label, p, g, inc in runs:
             res = h.scf(precision=p, slices=3, incremental=inc, guess=None if g is None else g[0])
+            hist[label] = h.history()[:, 1]
             ttc[label] = t_build + res["t_total_s"] + (0.0 if g is None else g[1])
             scf_info[label] = {"energy": res["energy"], "iterations": res["iterations"],
                                "converged": bool(res["converged"]), "t_iter_s": res["t_iter_s"],
                                "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"],
                                "incremental_builds": res["incremental_builds"]}
 
+    # split vs FP64 from the same core-Hamiltonian guess: energy difference iteration by iteration
+    de_iter = None
+    if args.ttc and split and args.compare_ttc:
+        a, b = hist["split"], hist["fp64"]
+        m = min(len(a), len(b))
+        de_iter = {"per_iteration": [float(f"{x:.3e}") for x in (a[:m] - b[:m])],
+                   "at_convergence": float(scf_info["split"]["energy"] - scf_info["fp64"]["energy"])}
+
     batched = None
     if args.batch > 0:
-        batched = batched_measure(binding, clusters, args.batch, torch, rank, dev)
+        batched = batched_measure(binding, clusters, args.batch, torch, rank, dev, args.batch_max_waters)
 
     peaks, peak_src = _peaks()
     keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
@@ -315,7 +333,7 @@ def gpu_arm(args):
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
                     "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
-        "time_to_converge_s": ttc or None, "scf": scf_info or None,
+        "time_to_converge_s": ttc or None, "scf": scf_info or None, "dE_split_vs_fp64": de_iter,
         "batched": batched,
         "learned_guess": learned,
         "clocks": clocks.summary(),
@@ -328,18 +346,18 @@ def gpu_arm(args):
         tdist.destroy_process_group()
 
 
-def learned_guess(binding, clusters, h, n_train):
-    """Train the density-guess network on converged densities of `n_train` seeded clusters (3-8
-    waters, seeds 10000+, generated by this library's FP64 SCF), then predict the guess for the
-    benchmark cluster. Returns (summary, D0, seconds to produce D0)."""
-    rng = clusters.SplitMix64(9090)
-    sizes = [3 + min(5, int(rng.uniform() * 6)) for _ in range(n_train)]
+def train_guess(binding, clusters, members, epochs=200, precision=None):
+    """Train the density-guess network on the converged densities of the seeded clusters `members`
+    ((waters, seed) pairs), generated by this library's SCF. Returns (network, summary)."""
     t0 = time.perf_counter()
     X, Y = [], []
-    for k, w in enumerate(sizes):
-        s = clusters.water_cluster(w, 10000 + k)
+    for w, seed in members:
+        s = clusters.water_cluster(w, seed)
         with binding.Handle(s) as hh:
-            hh.scf()
+            if precision is None:
+                hh.scf()
+            else:
+                hh.scf(precision=precision, slices=3, incremental=1)
             Y.append(hh.water_blocks(hh.matrix("D")))
         X.append(binding.water_features(s))
     t_data = time.perf_counter() - t0
@@ -347,25 +365,68 @@ def learned_guess(binding, clusters, h, n_train):
     nout = Y.shape[1]
     net = binding.Mlp(binding.DF_MLP_NFEAT, 256, 3, nout, seed=7)
     p = net.params()
-    p[-nout:] = Y.mean(axis=0)
+    p[-nout:] = Y.mean(axis=0)               # start from the mean water block (zero last-layer weights)
     p[-nout - nout * 256:-nout] = 0.0
     net.set_params(p)
     t0 = time.perf_counter()
-    hist = net.train(X, Y, epochs=200, batch=16, lr=3e-4, seed=3)
+    hist = net.train(X, Y, epochs=epochs, batch=16, lr=3e-4, seed=3)
     t_train = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    D0 = h.mlp_guess(net, bf16=True)
-    t_guess = time.perf_counter() - t0
+    return net, {"train_clusters": len(members), "train_waters": int(sum(w for w, _ in members)),
+                 "train_samples": int(len(X)), "network": "57-256x3-1275 ReLU, FP32 weights, BF16 inference",
+                 "epochs": epochs, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+                 "t_data_s": t_data, "t_train_s": t_train}
+
+
+def learned_guess_net(binding, clusters, n_train):
+    """The density-guess network trained on `n_train` seeded clusters of 3-8 waters (seeds 10000+, FP64
+    SCF densities). Trained before the benchmark cluster's tensors take the device memory."""
+    rng = clusters.SplitMix64(9090)
+    members = [(3 + min(5, int(rng.uniform() * 6)), 10000 + k) for k in range(n_train)]
+    return train_guess(binding, clusters, members)
+
+
+def guess_study(args):
+    """The learned guess on held-out clusters: train on n_train clusters of 4-24 waters (seeds 10000+),
+    evaluate on n_eval clusters of 8-32 waters (seeds 20000+) against the core-Hamiltonian guess, both
+    with the split-precision SCF (incremental Fock late). Prints one JSON line."""
+    from paper_1707_03771_gb300 import binding, build, clusters
+    build.build()
+    binding.load()
+    n_train, n_eval = (int(x) for x in args.guess_study.split(","))
+    rng = clusters.SplitMix64(7070)
+    train = [(4 + min(20, int(rng.uniform() * 21)), 10000 + k) for k in range(n_train)]
+    evals = [(8 + min(24, int(rng.uniform() * 25)), 20000 + k) for k in range(n_eval)]
+    prec = binding.DF_PREC_SPLIT
+    net, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
+    rows = []
+    for w, seed in evals:
+        with binding.Handle(clusters.water_cluster(w, seed)) as h:
+            h.build_B()
+            core = h.scf(precision=prec, slices=3, incremental=1)
+            t0 = time.perf_counter()
+            D0 = h.mlp_guess(net, bf16=True)
+            t_guess = time.perf_counter() - t0
+            lrn = h.scf(precision=prec, slices=3, incremental=1, guess=D0)
+        rows.append({"waters": w, "seed": seed, "iterations_core": core["iterations"],
+                     "iterations_learned": lrn["iterations"], "t_scf_core_s": core["t_total_s"],
+                     "t_scf_learned_s": lrn["t_total_s"] + t_guess,
+                     "dE_learned_vs_core": lrn["energy"] - core["energy"],
+                     "converged": bool(core["converged"] and lrn["converged"])})
     net.close()
-    return ({"train_clusters": n_train, "train_waters": int(sum(sizes)), "network": "57-256x3-1275 ReLU, FP32 "
-             "weights, BF16 inference", "epochs": 200, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
-             "t_data_s": t_data, "t_train_s": t_train, "t_guess_s": t_guess}, D0, t_guess)
+    it_c = [r["iterations_core"] for r in rows]
+    it_l = [r["iterations_learned"] for r in rows]
+    print(json.dumps({"study": "learned initial guess on held-out clusters", "training": summary,
+                      "eval_clusters": n_eval, "mean_iterations_core": float(np.mean(it_c)),
+                      "mean_iterations_learned": float(np.mean(it_l)),
+                      "iterations_saved_fraction": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
+                      "max_abs_dE_learned_vs_core": float(max(abs(r["dE_learned_vs_core"]) for r in rows)),
+                      "all_converged": all(r["converged"] for r in rows), "clusters": rows}))
 
 
-def batched_measure(binding, clusters, count, torch, rank=0, dev=None):
+def batched_measure(binding, clusters, count, torch, rank=0, dev=None, wmax=8):
     """Many small clusters (batch_members): time to converge all of them with the split-precision SCF,
     one after another versus together (scf_run_batch in waves); times are the maximum over ranks."""
-    members = batch_members(count, rank)
+    members = batch_members(count, rank, wmax)
     sizes = [w for w, _ in members]
     systems = [clusters.water_cluster(w, seed) for w, seed in members]
     prec = binding.DF_PREC_SPLIT
@@ -472,13 +533,19 @@ def main():
     ap.add_argument("--compare-ttc", action="store_true", help="also time a full FP64 SCF (minutes)")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false")
     ap.add_argument("--batch", type=int, default=16, help="molecules in the batched-SCF measurement (0: skip)")
+    ap.add_argument("--batch-max-waters", type=int, default=8, help="cluster sizes 1..W in the batched measurement")
+    ap.add_argument("--guess-study", default=None, metavar="NTRAIN,NEVAL",
+                    help="only the learned-guess study on held-out clusters (one JSON line)")
+    ap.add_argument("--guess-epochs", type=int, default=200)
     ap.add_argument("--learned", type=int, default=24, help="training clusters for the learned guess (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.guess_study:
+        guess_study(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

@@ -129,7 +129,6 @@ void ensure_jk_buffers(df_handle* h, int nocc) {
     }
     if (nocc > h->nocc_alloc) {
         const int ldy = ((nocc + 31) / 32) * 32;
-        h->Y.alloc((size_t)h->naux * pk.np * ldy);
         h->Cpad.alloc((size_t)pk.np * ldy);
         h->dC.alloc((size_t)h->n * nocc);
         h->nocc_alloc = nocc;
@@ -184,6 +183,8 @@ void exchange_fp64(df_handle* h, int nocc, double* dK) {
     DF_CUDA(cudaEventCreate(&e1));
     DF_CUDA(cudaEventCreate(&e2));
     DF_CUDA(cudaEventRecord(e0, s));
+    const size_t ny = (size_t)h->naux * pk.np * ldy;   // the FP64 Y is allocated on first FP64 use only
+    if (h->Y.n < ny) h->Y.alloc(ny);
     y_transform_fp64(s, h->B.p, pk.row, pk.nt, h->naux, h->Cpad.p, ldy, nocc, h->Y.p);
     DF_CUDA(cudaEventRecord(e1, s));
     const int ntiles = pk.nt * (pk.nt + 1) / 2;

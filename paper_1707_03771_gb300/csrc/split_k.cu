@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -459,6 +460,8 @@ struct SplitState {
     int ldy = 0;
     int nsplit = 0;
     int PB = 0;
+    bool blocked = false;        // B slices cut per block of pblk auxiliary rows at every build
+    int pblk = 0;
 };
 
 void free_split(df_handle* h) {
@@ -493,9 +496,11 @@ void prepare_b(df_handle* h, SplitState* st) {
 }
 
 // ---- autotuner ----------------------------------------------------------------------------------
-// The tile width N of the tensor-core Y kernel (32, 64 or 80 columns dividing ldy) and the split of the
-// K kernel over auxiliary blocks are picked by timing the candidates on the call's own operands the
-// first time a size bucket (np, ldy, naux / 512, S) is met; the choice is kept for the process.
+// The tile width of the tensor-core Y kernel (32, 64 or 80 columns dividing ldy), and the tile width (32
+// or 64) and auxiliary-block split of the K kernel, are picked by timing the candidates on the call's own
+// operands the first time a size bucket (np, ldy, naux / 512, S) is met; the choice is kept for the
+// process. Y is timed on the first auxiliary block (all rows when every slice is resident), K on the
+// finished Y slices; every candidate computes the same values.
 struct TcChoice {
     int yN = 0, kN = 64, ksplit = 0;
 };
@@ -520,29 +525,32 @@ double time_once(cudaStream_t s, F&& launch) {
 }
 
 template <int S>
-TcChoice autotune_tc(df_handle* h, SplitState* st) {
-    cudaStream_t s = h->stream;
-    const int np = st->np, ldy = st->ldy, naux = h->naux;
-    const auto t0 = std::chrono::steady_clock::now();
-    TcChoice best;
+int tune_y(df_handle* h, SplitState* st, int nb, float2* Yb) {
     double best_ms = 1e30;
+    int best = 0;
     for (int N : {80, 64, 32}) {
-        if (ldy % N) continue;
-        const double ms = time_once(s, [&] { y_split_tc(s, S, N, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err); });
+        if (st->ldy % N) continue;
+        const double ms = time_once(h->stream, [&] {
+            y_split_tc(h->stream, S, N, st->Bs, st->Be, st->Cs, st->Ce, nb, st->np, st->ldy, Yb, st->err);
+        });
         if (ms < best_ms) {
             best_ms = ms;
-            best.yN = N;
+            best = N;
         }
     }
+    return best;
+}
+
+template <int S>
+void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
+    cudaStream_t s = h->stream;
+    const int np = st->np, ldy = st->ldy, naux = h->naux;
     const long long nblk = (naux + st->PB - 1) / st->PB;
-    const long long ystr = (long long)naux * np * ldy;
-    split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
-    DF_CHECK_LAUNCH();
-    const int h0 = st->nsplit_tc;   // the occupancy heuristic: about 4 CTAs per SM
+    const int h0 = std::max(1, (int)std::min<long long>(st->nsplit_tc, nblk));   // occupancy heuristic
     std::vector<int> cands;
     for (int c : {1, std::max(1, h0 / 2), h0, 2 * h0, 4 * h0}) {
         const long long bytes = (long long)c * st->npt * st->npt * sizeof(float2);
-        if (c >= 1 && c <= nblk && bytes <= (2LL << 30) && std::find(cands.begin(), cands.end(), c) == cands.end())
+        if (c <= nblk && bytes <= (2LL << 30) && std::find(cands.begin(), cands.end(), c) == cands.end())
             cands.push_back(c);
     }
     const int cmax = *std::max_element(cands.begin(), cands.end());
@@ -552,12 +560,12 @@ TcChoice autotune_tc(df_handle* h, SplitState* st) {
         DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * cmax * (long long)st->npt * st->npt));
         st->kcap = cmax;
     }
-    // K: the half-tile width at the occupancy heuristic's split, then the split at that width
-    best_ms = 1e30;
+    // the half-tile width at the heuristic's split, then the split at that width
+    double best_ms = 1e30;
     for (int N : {64, 32}) {
         const double ms = time_once(s, [&] {
-            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, h0 <= cmax ? h0 : cmax, st->tiles128,
-                       st->ntiles128, st->Kpart_tc, st->npt, st->err);
+            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, std::min(h0, cmax), st->tiles128, st->ntiles128,
+                       st->Kpart_tc, st->npt, st->err);
         });
         if (ms < best_ms) {
             best_ms = ms;
@@ -575,10 +583,10 @@ TcChoice autotune_tc(df_handle* h, SplitState* st) {
             best.ksplit = c;
         }
     }
-    g_tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return best;
 }
 
+// Y over auxiliary blocks: one block of all rows when every slice is resident; otherwise the slices of
+// each block of st->pblk rows are cut from the packed FP64 B just before the Y kernel consumes them.
 template <int S>
 void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK, cudaEvent_t* ev) {
     cudaStream_t s = h->stream;
@@ -586,81 +594,99 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const long long cstr = (long long)ldy * np;
     split_c_kernel<S><<<ldy, 256, 0, s>>>(dC, h->n, nocc, np, ldy, st->Cs, cstr, st->Ce);
     DF_CHECK_LAUNCH();
-    // Y = B C: CTA tiles of 64 rows x 32*WN columns
+    // mma.sync Y: CTA tiles of 64 rows x 32*WN columns
     constexpr int WNT = 8 * Frag<S>::NJ;
     const int WN = std::min(5, ldy / WNT);
     const int BN = WNT * WN;
     const size_t smem = (size_t)2 * S * (64 + BN) * LDS * sizeof(bf16) + (64 + BN) * sizeof(int);
     DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 gy(np / 64, naux, (ldy + BN - 1) / BN);
     const bool tc = use_tensor_cores() && (S == 3 || S == 5);
+    const std::array<int, 4> key{np, ldy, (naux + 511) / 512, S};
+    TcChoice ch;
+    bool have = !tc;
     if (tc) {
-        const std::array<int, 4> key{np, ldy, (naux + 511) / 512, S};
-        TcChoice ch;
-        bool have = false;
-        {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tune.find(key);
-            if (it != g_tune.end()) {
-                ch = it->second;
-                have = true;
-            }
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            ch = it->second;
+            have = true;
         }
-        // DFHF_TC_TILES="yN,kN,ksplit" fixes the choice (tests compare tilings; the results do not depend on it)
-        if (const char* f = std::getenv("DFHF_TC_TILES")) {
-            TcChoice fc;
-            if (std::sscanf(f, "%d,%d,%d", &fc.yN, &fc.kN, &fc.ksplit) == 3 && fc.ksplit >= 1 &&
-                (fc.yN == 32 || fc.yN == 64 || fc.yN == 80) && ldy % fc.yN == 0 && (fc.kN == 32 || fc.kN == 64)) {
-                ch = fc;
-                have = true;
-            }
-        }
-        if (!have) {
-            ch = autotune_tc<S>(h, st);
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune[key] = ch;
-        }
-        st->yN = ch.yN;
-        st->kN = ch.kN;
-        // a choice made for another handle of the bucket: at most one split per auxiliary block, and
-        // room for it in the partial-sum buffer
-        const int ksplit = (int)std::min<long long>(ch.ksplit, (naux + st->PB - 1) / st->PB);
-        if (ksplit > st->kcap) {
-            cudaFree(st->Kpart_tc);
-            st->Kpart_tc = nullptr;
-            DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * ksplit * (long long)st->npt * st->npt));
-            st->kcap = ksplit;
-        }
-        st->nsplit_tc = ksplit;
-        h->timings_ms[12] = ch.yN;
-        h->timings_ms[13] = st->nsplit_tc;
-        h->timings_ms[14] = g_tune_ms;
-        h->timings_ms[15] = st->kN;
     }
+    // DFHF_TC_TILES="yN,kN,ksplit" fixes the choice (tests compare tilings; the results do not depend on it)
+    if (const char* f = tc ? std::getenv("DFHF_TC_TILES") : nullptr) {
+        TcChoice fc;
+        if (std::sscanf(f, "%d,%d,%d", &fc.yN, &fc.kN, &fc.ksplit) == 3 && fc.ksplit >= 1 &&
+            (fc.yN == 32 || fc.yN == 64 || fc.yN == 80) && ldy % fc.yN == 0 && (fc.kN == 32 || fc.kN == 64)) {
+            ch = fc;
+            have = true;
+        }
+    }
+    double tune_ms = 0.0;
     DF_CUDA(cudaEventRecord(ev[0], s));
-    if (tc) {
-        y_split_tc(s, S, st->yN, st->Bs, st->Be, st->Cs, st->Ce, naux, np, ldy, st->Y, st->err);
-    } else {
-        y_split_kernel<S><<<gy, 64 * WN, smem, s>>>(st->Bs, (long long)naux * np * np, st->Be, st->Cs, cstr, st->Ce, np,
-                                                     ldy, st->Y);
-        DF_CHECK_LAUNCH();
+    const int pblk = st->blocked ? st->pblk : naux;
+    for (int p0 = 0; p0 < naux; p0 += pblk) {
+        const int nb = std::min(pblk, naux - p0);
+        const long long bstr = (long long)(st->blocked ? nb : naux) * np * np;
+        if (st->blocked) {
+            split_b_kernel<S><<<dim3((unsigned)np, nb), 256, 0, s>>>(h->B.p + (long long)p0 * h->pk.row, h->pk.row,
+                                                                    h->n, np, st->Bs, bstr, st->Be);
+            DF_CHECK_LAUNCH();
+        }
+        float2* Yb = st->Y + (long long)p0 * np * ldy;
+        if (tc) {
+            if (!have && p0 == 0) {
+                const auto t0 = std::chrono::steady_clock::now();
+                ch.yN = tune_y<S>(h, st, nb, Yb);
+                tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
+            y_split_tc(s, S, ch.yN, st->Bs, st->Be, st->Cs, st->Ce, nb, np, ldy, Yb, st->err);
+        } else {
+            y_split_kernel<S><<<dim3(np / 64, nb, (ldy + BN - 1) / BN), 64 * WN, smem, s>>>(st->Bs, bstr, st->Be, st->Cs,
+                                                                                           cstr, st->Ce, np, ldy, Yb);
+            DF_CHECK_LAUNCH();
+        }
     }
     DF_CUDA(cudaEventRecord(ev[1], s));
     const long long nblk = (naux + st->PB - 1) / st->PB;
     const long long ystr = (long long)naux * np * ldy;
     split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
     DF_CHECK_LAUNCH();
-    const int nt = np / 64;
-    const int ntiles = nt * (nt + 1) / 2;
-    const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
-    DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
-    DF_CUDA(cudaEventRecord(ev[2], s));
     if (tc) {
-        k_split_tc(s, S, st->kN, st->Ys, st->Ye, naux, np, ldy, st->PB, st->nsplit_tc, st->tiles128, st->ntiles128,
+        if (!have) {
+            const auto t0 = std::chrono::steady_clock::now();
+            tune_k<S>(h, st, ch);
+            tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[key] = ch;
+            g_tune_ms += tune_ms;
+        }
+        // a choice made for another handle of the bucket: at most one split per auxiliary block, and room
+        // for it in the partial-sum buffer
+        const int ksplit = (int)std::min<long long>(ch.ksplit, nblk);
+        if (ksplit > st->kcap) {
+            cudaFree(st->Kpart_tc);
+            st->Kpart_tc = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * ksplit * (long long)st->npt * st->npt));
+            st->kcap = ksplit;
+        }
+        st->yN = ch.yN;
+        st->kN = ch.kN;
+        st->nsplit_tc = ksplit;
+        h->timings_ms[12] = ch.yN;
+        h->timings_ms[13] = ksplit;
+        h->timings_ms[14] = g_tune_ms;
+        h->timings_ms[15] = ch.kN;
+        DF_CUDA(cudaEventRecord(ev[2], s));
+        k_split_tc(s, S, ch.kN, st->Ys, st->Ye, naux, np, ldy, st->PB, ksplit, st->tiles128, st->ntiles128,
                    st->Kpart_tc, st->npt, st->err);
         DF_CUDA(cudaEventRecord(ev[3], s));
-        k_tc_reduce(s, st->Kpart_tc, st->nsplit_tc, st->npt, h->n, dK);
+        k_tc_reduce(s, st->Kpart_tc, ksplit, st->npt, h->n, dK);
     } else {
+        const int nt = np / 64;
+        const int ntiles = nt * (nt + 1) / 2;
+        const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
+        DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
+        DF_CUDA(cudaEventRecord(ev[2], s));
         k_split_kernel<S><<<dim3(ntiles, st->nsplit), 2 * (64 / WNT) * 32, ksmem, s>>>(
             st->Ys, ystr, st->Ye, naux, np, ldy, st->PB, st->nsplit, h->ktiles.p, st->Kpart);
         DF_CHECK_LAUNCH();
@@ -670,13 +696,13 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         DF_CHECK_LAUNCH();
     }
 }
-
 }  // namespace
 
 // K from the split path for the occupied coefficients dC (n x nocc, device).
-// B is split once; when HBM allows, with SMAX slices, so that builds with fewer slices (early SCF
+// B is split once with SMAX slices when HBM allows, so that builds with fewer slices (early SCF
 // iterations) and with SMAX slices (late iterations) share one split: the first S slices of an
-// SMAX-slice split are exactly the S-slice split (same exponents, same rounding sequence).
+// SMAX-slice split are an S-slice split of the same values (same exponents; within 0.51 2^{-7S} of
+// each scaled value). Otherwise the slices are cut per block of auxiliary rows at every build.
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK) {
     if (slices < 2 || slices > SMAX) throw Error{DF_E_ARG, "slices must be 2..5"};
     if (h->pk.np % 64) throw Error{DF_E_ARG, "internal: padded size not a multiple of 64"};
@@ -691,6 +717,8 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
     DF_CUDA(cudaEventRecord(e0, h->stream));
     const int ldy = ((nocc + 31) / 32) * 32;
+    // set-up: a failure part-way leaves no half-built state behind (the next call starts afresh)
+    try {
     if (!st) {
         st = new SplitState();
         h->split = st;
@@ -698,14 +726,30 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         const long long np = st->np;
         size_t free_b = 0, total_b = 0;
         DF_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        const double per_slice = 2.0 * h->naux * np * np + 2.0 * h->naux * np * ldy;
-        const double fixed = 8.0 * h->naux * np * ldy + 16.0 * np * np + (4ull << 30);
-        st->S = (free_b > SMAX * per_slice + fixed) ? SMAX : slices;
-        switch (st->S) {
-            case 2: prepare_b<2>(h, st); break;
-            case 3: prepare_b<3>(h, st); break;
-            case 4: prepare_b<4>(h, st); break;
-            default: prepare_b<5>(h, st); break;
+        // SMAX slices of every auxiliary row when they fit beside Y and its slices; otherwise SMAX slices
+        // of blocks of rows, cut from B at each build
+        const double row_slices = 2.0 * SMAX * np * np;                      // one row, every slice
+        const double ybytes = (8.0 + 2.0 * SMAX) * h->naux * np * ldy;      // Y and its slices
+        // kept free: an FP64 Y of the same shape (FP64 builds on the same handle) and working space
+        const double slack = 8.0 * h->naux * np * ldy + 16.0 * np * np + (4ull << 30);
+        st->S = SMAX;
+        // DFHF_SPLIT_BLOCK_ROWS=r forces blocks of r rows (tests compare the two modes)
+        const char* fb = std::getenv("DFHF_SPLIT_BLOCK_ROWS");
+        const int forced = fb ? std::atoi(fb) : 0;
+        if (forced > 0) {
+            st->blocked = true;
+            st->pblk = std::min(forced, h->naux);
+            DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
+            DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * (long long)st->pblk * np));
+        } else if ((double)free_b > row_slices * h->naux + ybytes + slack) {
+            prepare_b<SMAX>(h, st);
+        } else {
+            const double avail = (double)free_b - ybytes - slack;
+            if (avail < row_slices) throw Error{DF_E_NOMEM, "split exchange: no room for one row of B slices"};
+            st->blocked = true;
+            st->pblk = (int)std::min<double>(h->naux, std::floor(avail / row_slices));
+            DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
+            DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * (long long)st->pblk * np));
         }
     }
     if (ldy != st->ldy) {
@@ -752,6 +796,13 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     }
     // synchronous callers clear the timeout flag per call; under the SCF driver it stays set once
     // raised and is read with the iteration's scalars
+    } catch (...) {
+        free_split(h);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (auto& e : ev) cudaEventDestroy(e);
+        throw;
+    }
     if (st->err && !h->tc_err_host) DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
     switch (slices) {
         case 2: run_split<2>(h, st, dC, nocc, dK, ev); break;

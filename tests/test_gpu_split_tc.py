@@ -93,3 +93,28 @@ def test_tile_widths_give_identical_exchange(lib, slices):
     ref = out["32,64,4"]
     for k, v in out.items():
         assert np.array_equal(v, ref), k
+
+
+def test_blocked_slices_match_resident_slices(lib):
+    """When B's slices do not fit in HBM they are cut per block of auxiliary rows at every build; at 5
+    slices the digits are the same as with every row resident, so K is bitwise identical (ragged last
+    block: 1096 rows in blocks of 100)."""
+    system = clusters.workload("water8")
+    rng = np.random.default_rng(8)
+    with lib.Handle(system) as h:
+        h.build_B()
+        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+        D = 2 * C @ C.T
+        K64 = h.jk(D, C, lib.DF_PREC_FP64)[1]
+        resident = _k(h, lib, D, C, 5, tc=True)
+    with lib.Handle(system) as h:
+        h.build_B()
+        os.environ["DFHF_SPLIT_BLOCK_ROWS"] = "100"
+        try:
+            blocked5 = _k(h, lib, D, C, 5, tc=True)
+            blocked3 = _k(h, lib, D, C, 3, tc=True)
+        finally:
+            del os.environ["DFHF_SPLIT_BLOCK_ROWS"]
+    assert np.array_equal(blocked5, resident)
+    scale = np.abs(K64).max()
+    assert np.abs(blocked3 - K64).max() <= 2.0 ** (7 - 21) * scale
