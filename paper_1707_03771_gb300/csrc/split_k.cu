@@ -75,33 +75,82 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
 }
 
 // ------------------------------------------------------------------------------------------------
-// one-time split of B: packed FP64 rows -> Bs[s][P][mu][nu] (np x np per P), exponent per (P, mu)
+// split of B: packed FP64 tiles -> Bs[s][P][mu][nu] (np x np per P), exponent per (P, mu)
 // ------------------------------------------------------------------------------------------------
-template <int S>
-__global__ void __launch_bounds__(256) split_b_kernel(const double* __restrict__ B, long long row, int n, int np,
-                                                      bf16* __restrict__ Bs, long long sstride,
-                                                      int* __restrict__ Be) {
-    const int mu = blockIdx.x;
-    const long long P = blockIdx.y;
-    const double* Bp = B + P * row;
-    double mx = 0.0;
-    if (mu < n)
-        for (int nu = threadIdx.x; nu < n; nu += blockDim.x) mx = fmax(mx, fabs(Bp[packed_index(mu, nu)]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+// tile pair index -> (I, J), I >= J
+__device__ __forceinline__ void tile_of(long long tp, int& I, int& J) {
+    I = (int)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
+    while ((long long)(I + 1) * (I + 2) / 2 <= tp) ++I;
+    while ((long long)I * (I + 1) / 2 > tp) --I;
+    J = (int)(tp - (long long)I * (I + 1) / 2);
+}
+
+// rmax[P][mu] = max_nu |B_P[mu][nu]| as the bit pattern of a non-negative double (ordered like the
+// value), gathered tile by tile: rows of tile (I, J) for mu in I, its columns for mu in J (I > J)
+__global__ void __launch_bounds__(256) row_max_tiles_kernel(const double* __restrict__ B, long long row, int np,
+                                                            unsigned long long* __restrict__ rmax) {
+    __shared__ double tile[64][65];
+    const long long tp = blockIdx.x, P = blockIdx.y;
+    int I, J;
+    tile_of(tp, I, J);
+    const double* src = B + P * row + tp * 4096;
+    for (int i = threadIdx.x; i < 4096; i += 256) tile[i >> 6][i & 63] = fabs(src[i]);
     __syncthreads();
-    mx = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    const int k = threadIdx.x >> 2, q = threadIdx.x & 3;   // row (or column) k, quarter q
+    double mr = 0.0, mc = 0.0;
+#pragma unroll 4
+    for (int j = q * 16; j < q * 16 + 16; ++j) {
+        mr = fmax(mr, tile[k][j]);
+        mc = fmax(mc, tile[j][k]);
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+        mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    }
+    if (q == 0) {
+        unsigned long long* rm = rmax + P * np;
+        atomicMax(rm + I * 64 + k, (unsigned long long)__double_as_longlong(mr));
+        if (I != J) atomicMax(rm + J * 64 + k, (unsigned long long)__double_as_longlong(mc));
+    }
+}
+
+// Be[i] = e with max |row| 2^-e < 1 (0 for a zero row)
+__global__ void row_exponent_kernel(const unsigned long long* __restrict__ rmax, long long count, int* __restrict__ Be) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double mx = __longlong_as_double((long long)rmax[i]);
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
-    if (threadIdx.x == 0) Be[P * np + mu] = e;
-    bf16* out = Bs + (P * np + mu) * (long long)np;
-    for (int nu = threadIdx.x; nu < np; nu += blockDim.x) {
-        const double x = (mu < n && nu < n) ? Bp[packed_index(mu, nu)] : 0.0;
-        split_pow2<S>(x, e, out + nu, sstride);
+    Be[i] = e;
+}
+
+// slices of rows [0, nrows) of B (pointer at the block's first row): each packed tile (I, J) is read
+// once and written as block (I, J) and, for I > J, transposed as block (J, I); Be holds the block's rows
+template <int S>
+__global__ void __launch_bounds__(256) split_b_tiles_kernel(const double* __restrict__ B, long long row, int np,
+                                                            const int* __restrict__ Be, bf16* __restrict__ Bs,
+                                                            long long sstride) {
+    __shared__ double tile[64][65];
+    const long long tp = blockIdx.x, P = blockIdx.y;
+    int I, J;
+    tile_of(tp, I, J);
+    const double* src = B + P * row + tp * 4096;
+    for (int i = threadIdx.x; i < 4096; i += 256) tile[i >> 6][i & 63] = src[i];
+    __syncthreads();
+    const int* e = Be + P * np;
+    bf16* out = Bs + P * np * (long long)np;
+    for (int i = threadIdx.x; i < 4096; i += 256) {   // block (I, J): mu = I*64 + r, nu = J*64 + c
+        const int r = i >> 6, c = i & 63;
+        const int mu = I * 64 + r;
+        split_pow2<S>(tile[r][c], e[mu], out + (long long)mu * np + J * 64 + c, sstride);
     }
+    if (I != J)
+        for (int i = threadIdx.x; i < 4096; i += 256) {   // block (J, I): mu = J*64 + c, nu = I*64 + r
+            const int r = i & 63, c = i >> 6;
+            const int mu = J * 64 + c;
+            split_pow2<S>(tile[r][c], e[mu], out + (long long)mu * np + I * 64 + r, sstride);
+        }
 }
 
 // C (n x nocc row-major) -> Cs[s][i][nu] (ldy x np), exponent per column i
@@ -484,15 +533,36 @@ void free_split(df_handle* h) {
 
 namespace {
 
+// exponent of every row (P, mu) of B, from the packed tiles (B does not change for the handle)
+void row_exponents(df_handle* h, SplitState* st) {
+    if (h->naux > 65535) throw Error{DF_E_ARG, "split exchange supports at most 65535 auxiliary functions"};
+    const long long count = (long long)h->naux * st->np;
+    DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * count));
+    DevBuf<unsigned long long> rmax;
+    rmax.alloc(count);
+    rmax.zero(h->stream);
+    row_max_tiles_kernel<<<dim3((unsigned)h->pk.ntp, h->naux), 256, 0, h->stream>>>(h->B.p, h->pk.row, st->np, rmax.p);
+    DF_CHECK_LAUNCH();
+    row_exponent_kernel<<<nblocks(count, 256), 256, 0, h->stream>>>(rmax.p, count, st->Be);
+    DF_CHECK_LAUNCH();
+    DF_CUDA(cudaStreamSynchronize(h->stream));   // rmax is released on return
+}
+
+// slices of auxiliary rows [p0, p0 + nb) into Bs (block-local rows)
+template <int S>
+void slice_b_rows(df_handle* h, SplitState* st, int p0, int nb, long long bstr) {
+    split_b_tiles_kernel<S><<<dim3((unsigned)h->pk.ntp, nb), 256, 0, h->stream>>>(
+        h->B.p + (long long)p0 * h->pk.row, h->pk.row, st->np, st->Be + (long long)p0 * st->np, st->Bs, bstr);
+    DF_CHECK_LAUNCH();
+}
+
 template <int S>
 void prepare_b(df_handle* h, SplitState* st) {
     const long long np = st->np;
     const long long bstr = (long long)h->naux * np * np;
     DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * S * bstr));
-    DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * h->naux * np));
-    split_b_kernel<S><<<dim3((unsigned)np, h->naux), 256, 0, h->stream>>>(h->B.p, h->pk.row, h->n, (int)np, st->Bs, bstr,
-                                                                        st->Be);
-    DF_CHECK_LAUNCH();
+    row_exponents(h, st);
+    slice_b_rows<S>(h, st, 0, h->naux, bstr);
 }
 
 // ---- autotuner ----------------------------------------------------------------------------------
@@ -627,11 +697,8 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     for (int p0 = 0; p0 < naux; p0 += pblk) {
         const int nb = std::min(pblk, naux - p0);
         const long long bstr = (long long)(st->blocked ? nb : naux) * np * np;
-        if (st->blocked) {
-            split_b_kernel<S><<<dim3((unsigned)np, nb), 256, 0, s>>>(h->B.p + (long long)p0 * h->pk.row, h->pk.row,
-                                                                    h->n, np, st->Bs, bstr, st->Be);
-            DF_CHECK_LAUNCH();
-        }
+        if (st->blocked) slice_b_rows<S>(h, st, p0, nb, bstr);
+        const int* Beb = st->Be + (long long)p0 * np;   // row exponents of the block
         float2* Yb = st->Y + (long long)p0 * np * ldy;
         if (tc) {
             if (!have && p0 == 0) {
@@ -639,9 +706,9 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
                 ch.yN = tune_y<S>(h, st, nb, Yb);
                 tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             }
-            y_split_tc(s, S, ch.yN, st->Bs, st->Be, st->Cs, st->Ce, nb, np, ldy, Yb, st->err);
+            y_split_tc(s, S, ch.yN, st->Bs, Beb, st->Cs, st->Ce, nb, np, ldy, Yb, st->err);
         } else {
-            y_split_kernel<S><<<dim3(np / 64, nb, (ldy + BN - 1) / BN), 64 * WN, smem, s>>>(st->Bs, bstr, st->Be, st->Cs,
+            y_split_kernel<S><<<dim3(np / 64, nb, (ldy + BN - 1) / BN), 64 * WN, smem, s>>>(st->Bs, bstr, Beb, st->Cs,
                                                                                            cstr, st->Ce, np, ldy, Yb);
             DF_CHECK_LAUNCH();
         }
@@ -740,7 +807,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
             st->blocked = true;
             st->pblk = std::min(forced, h->naux);
             DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
-            DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * (long long)st->pblk * np));
+            row_exponents(h, st);
         } else if ((double)free_b > row_slices * h->naux + ybytes + slack) {
             prepare_b<SMAX>(h, st);
         } else {
@@ -749,7 +816,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
             st->blocked = true;
             st->pblk = (int)std::min<double>(h->naux, std::floor(avail / row_slices));
             DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
-            DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * (long long)st->pblk * np));
+            row_exponents(h, st);
         }
     }
     if (ldy != st->ldy) {
