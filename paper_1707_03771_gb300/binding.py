@@ -276,7 +276,10 @@ def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, p
     out = (Result * n)()
     rc = load().scf_run_batch(hs, n, ctypes.byref(o), out)
     if rc not in (DF_OK, DF_E_NOTCONV):
-        raise DFError(rc, "scf_run_batch: " + load().df_last_error(handles[0].h).decode())
+        failed = [(i, out[i].status, load().df_last_error(handles[i].h).decode()) for i in range(n)
+                  if out[i].status not in (DF_OK, DF_E_NOTCONV)]
+        detail = "; ".join(f"molecule {i}: status {st}: {msg}" for i, st, msg in failed[:4])
+        raise DFError(rc, f"scf_run_batch: {len(failed)} of {n} failed: {detail}")
     return [out[i].as_dict() for i in range(n)]
 
 

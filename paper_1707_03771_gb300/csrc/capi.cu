@@ -563,7 +563,7 @@ void df_free(df_handle* h) {
     for (auto& c : h->aux_pairs) cudaFree(c.d_pairs);
     if (h->solver) cusolverDnDestroy(h->solver);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
-    // DevBuf members are released explicitly (they have no destructor so a copy cannot double free)
+    // device buffers released here, while the handle's device is current (their destructors then find them empty)
     DevBuf<double>* bufs[] = {&h->d_atom_xyz, &h->d_atom_Z, &h->S, &h->T, &h->V, &h->H, &h->metric, &h->Linv,
                               &h->A3c, &h->B, &h->Dw, &h->gamma, &h->Jp, &h->Y, &h->Kpart, &h->Cpad, &h->dD,
                               &h->dC, &h->dJ, &h->dK, &h->X, &h->F, &h->Fx, &h->Dm, &h->C, &h->eps, &h->work1,

@@ -80,8 +80,27 @@ __host__ __device__ inline long long packed_index(int mu, int nu) {
 // ------------------------------------------------------------------------------------------------
 template <class T>
 struct DevBuf {
+    // owns one device allocation: move-only, released by its owner's scope (or earlier by release())
     T* p = nullptr;
     size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
     void alloc(size_t count) {
         release();
         if (count == 0) return;

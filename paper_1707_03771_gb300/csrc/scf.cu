@@ -550,6 +550,9 @@ class ScfRun {
     }
 
     void release() {
+        // work this run queued (on an error path: copies into the pinned words, kernels on its buffers)
+        // completes before anything is freed
+        if (s_) cudaStreamSynchronize(s_);
         if (h_ && pin_ctl_ && h_->tc_err_host == pin_ctl_ + 2 * DIIS_MAX + 2) h_->tc_err_host = nullptr;
         if (work_) cudaFree(work_);
         if (info_) cudaFree(info_);

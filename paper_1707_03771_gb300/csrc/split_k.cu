@@ -511,11 +511,15 @@ struct SplitState {
     int PB = 0;
     bool blocked = false;        // B slices cut per block of pblk auxiliary rows at every build
     int pblk = 0;
+    // tile choice per slice count, fixed at this state's first build with that count (0: not yet):
+    // Y tile width, K tile width, K split; buffers sized for it are never reallocated under queued work
+    int ch_y[SMAX + 1] = {0}, ch_k[SMAX + 1] = {0}, ch_split[SMAX + 1] = {0};
 };
 
 void free_split(df_handle* h) {
     SplitState* st = h->split;
     if (!st) return;
+    cudaStreamSynchronize(h->stream);   // queued builds finish before their buffers go
     cudaFree(st->Bs);
     cudaFree(st->Be);
     cudaFree(st->Cs);
@@ -625,6 +629,7 @@ void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
     }
     const int cmax = *std::max_element(cands.begin(), cands.end());
     if (cmax > st->kcap) {
+        DF_CUDA(cudaStreamSynchronize(s));
         cudaFree(st->Kpart_tc);
         st->Kpart_tc = nullptr;
         DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * cmax * (long long)st->npt * st->npt));
@@ -674,20 +679,25 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const std::array<int, 4> key{np, ldy, (naux + 511) / 512, S};
     TcChoice ch;
     bool have = !tc;
-    if (tc) {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
-            ch = it->second;
-            have = true;
-        }
-    }
     // DFHF_TC_TILES="yN,kN,ksplit" fixes the choice (tests compare tilings; the results do not depend on it)
     if (const char* f = tc ? std::getenv("DFHF_TC_TILES") : nullptr) {
         TcChoice fc;
         if (std::sscanf(f, "%d,%d,%d", &fc.yN, &fc.kN, &fc.ksplit) == 3 && fc.ksplit >= 1 &&
             (fc.yN == 32 || fc.yN == 64 || fc.yN == 80) && ldy % fc.yN == 0 && (fc.kN == 32 || fc.kN == 64)) {
             ch = fc;
+            have = true;
+        }
+    }
+    if (tc && !have && st->ch_y[S]) {   // this state's own choice: stable across its builds
+        ch.yN = st->ch_y[S];
+        ch.kN = st->ch_k[S];
+        ch.ksplit = st->ch_split[S];
+        have = true;
+    } else if (tc && !have) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            ch = it->second;
             have = true;
         }
     }
@@ -724,13 +734,17 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
             tune_k<S>(h, st, ch);
             tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune[key] = ch;
+            g_tune.emplace(key, ch);   // the first tuned choice of a bucket stays
             g_tune_ms += tune_ms;
         }
         // a choice made for another handle of the bucket: at most one split per auxiliary block, and room
         // for it in the partial-sum buffer
         const int ksplit = (int)std::min<long long>(ch.ksplit, nblk);
+        st->ch_y[S] = ch.yN;
+        st->ch_k[S] = ch.kN;
+        st->ch_split[S] = ksplit;
         if (ksplit > st->kcap) {
+            DF_CUDA(cudaStreamSynchronize(s));   // nothing queued may still read the old buffer
             cudaFree(st->Kpart_tc);
             st->Kpart_tc = nullptr;
             DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * ksplit * (long long)st->npt * st->npt));
@@ -820,6 +834,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         }
     }
     if (ldy != st->ldy) {
+        DF_CUDA(cudaStreamSynchronize(h->stream));   // earlier builds may still read these buffers
         cudaFree(st->Cs);
         cudaFree(st->Ce);
         cudaFree(st->Y);
@@ -864,6 +879,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     // synchronous callers clear the timeout flag per call; under the SCF driver it stays set once
     // raised and is read with the iteration's scalars
     } catch (...) {
+        cudaStreamSynchronize(h->stream);   // nothing queued may still use the buffers freed here
         free_split(h);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -109,7 +109,9 @@ void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const 
     size_t free_b = 0, total_b = 0;
     DF_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const double col_bytes = (double)WS * kp * 2 + 4;
-    long long nc = (long long)std::min<double>((double)ncol, 0.4 * (double)free_b / col_bytes);
+    // the chunk's transposed slices: at most 8 GB (several molecules may whiten at once)
+    const double chunk_bytes = std::min(0.4 * (double)free_b, 8.0e9);
+    long long nc = (long long)std::min<double>((double)ncol, chunk_bytes / col_bytes);
     nc = std::min<long long>(nc, 1LL << 19) / 4096 * 4096;
     if (nc < 64) nc = std::min<long long>(ncol, 64);
     if (nc > ncol) nc = ncol;
@@ -121,6 +123,7 @@ void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const 
     eA.alloc(nc);
     err.alloc(1);
     err.zero(s);
+    try {
     slice_rows_kernel<<<naux, 256, 0, s>>>(Linv, naux, kp, Ls.p, (long long)naux * kp, eL.p);
     DF_CHECK_LAUNCH();
     const int bucket = (naux + 511) / 512;
@@ -165,6 +168,10 @@ void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const 
     DF_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     DF_CUDA(cudaStreamSynchronize(s));
     if (herr) throw Error{DF_E_TIMEOUT, "tensor-core whitening kernel timed out waiting on a barrier"};
+    } catch (...) {
+        cudaStreamSynchronize(s);   // queued kernels finish before the scratch buffers are released
+        throw;
+    }
 }
 
 }  // namespace dfhf
