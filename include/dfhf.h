@@ -74,6 +74,11 @@ typedef struct {
                                 eigenproblem) and built at 3 slices; D_ref is rebuilt in full every 8
                                 iterations. 0: every iteration builds K in full. */
     double screen_tau;       /* drop shell triples whose bound is below tau (0 = none) */
+    int approx_diag;         /* 1: late iterations (max|e| < 1e-4) rotate the previous orbitals by
+                                kappa_ia = F'_ia / (eps_a - eps_i) (approximate diagonalisation, Stewart,
+                                Csaszar and Pulay 1982) instead of a full eigensolve; every 8th late
+                                iteration diagonalises in full. The result is unchanged (convergence is
+                                tested on the exact commutator). 0: full eigensolve every iteration. */
 } df_options;
 
 typedef struct {
@@ -90,6 +95,7 @@ typedef struct {
     int n_dropped;           /* orbitals removed by canonical orthogonalisation */
     int ramp_iteration;      /* split mode: first iteration built with 5 slices (0 if never) */
     int incremental_builds;  /* iterations whose K was K[D_ref] + K[D - D_ref] (options.incremental) */
+    int approx_steps;        /* Roothaan steps taken by approximate diagonalisation (options.approx_diag) */
     double t_build_s;        /* df_build_B time within this call (0 if B was already built) */
     double t_iter_s;         /* total SCF iteration time */
     double t_jk_s;           /* time in J/K builds */

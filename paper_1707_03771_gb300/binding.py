@@ -35,7 +35,8 @@ class Shell(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("conv_E", ctypes.c_double), ("conv_err", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("guess", ctypes.c_int), ("precision", ctypes.c_int),
-                ("slices", ctypes.c_int), ("incremental", ctypes.c_int), ("screen_tau", ctypes.c_double)]
+                ("slices", ctypes.c_int), ("incremental", ctypes.c_int), ("screen_tau", ctypes.c_double),
+                ("approx_diag", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -43,7 +44,7 @@ class Result(ctypes.Structure):
                 ("e_coul", ctypes.c_double), ("e_exch", ctypes.c_double), ("last_dE", ctypes.c_double),
                 ("last_err", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("ramp_iteration", ctypes.c_int),
-                ("incremental_builds", ctypes.c_int), ("t_build_s", ctypes.c_double),
+                ("incremental_builds", ctypes.c_int), ("approx_steps", ctypes.c_int), ("t_build_s", ctypes.c_double),
                 ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double)]
 
     def as_dict(self):
@@ -183,9 +184,9 @@ class Handle:
         self._check(load().df_coulomb_noalloc(self.h, D_ptr, J_ptr), "df_coulomb_noalloc")
 
     def scf(self, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
-            incremental=0, screen_tau=0.0, guess=None):
+            incremental=0, screen_tau=0.0, guess=None, approx_diag=0):
         """SCF from the core-Hamiltonian guess, or from the natural orbitals of `guess` (n x n)."""
-        o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau)
+        o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau, approx_diag)
         r = Result()
         if guess is None:
             rc = load().scf_run(self.h, ctypes.byref(o), ctypes.byref(r))
@@ -268,11 +269,11 @@ class Handle:
 
 
 def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
-              screen_tau=0.0, incremental=0):
+              screen_tau=0.0, incremental=0, approx_diag=0):
     """Solve several molecules together (scf_run_batch); returns one result dict per handle."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[hd.h.value for hd in handles])
-    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau)
+    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau, approx_diag)
     out = (Result * n)()
     rc = load().scf_run_batch(hs, n, ctypes.byref(o), out)
     if rc not in (DF_OK, DF_E_NOTCONV):

@@ -396,7 +396,8 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
 
 int scf_run(df_handle* h, const df_options* opts, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
-    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
+        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     try {
@@ -410,7 +411,8 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out) {
 
 int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
-    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
+        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     try {
@@ -424,7 +426,8 @@ int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_res
 
 int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out) {
     if (!hs || nmol < 1 || !opts || !out) return DF_E_ARG;
-    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
+        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     int dev = -1;

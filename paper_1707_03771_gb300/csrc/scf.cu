@@ -31,6 +31,7 @@ constexpr int SPLIT_LATE_SLICES = 5;      // slices of the late split-precision 
 constexpr double SPLIT_RAMP_ERR = 1e-4;   // max|e| below which the late builds start
 constexpr int INC_SLICES = 3;             // slices of the density-change exchange builds (split mode)
 constexpr int INC_RESET = 8;              // iterations per reference density (one full build, then changes)
+constexpr int DIAG_RESET = 8;             // late iterations per full eigensolve when approximating the others
 
 __global__ void build_x_kernel(const double* __restrict__ U, const double* __restrict__ s, int n, int first, int nX,
                                double* __restrict__ X) {
@@ -224,6 +225,24 @@ __global__ void k_update_kernel(const double* __restrict__ Kref, const double* _
     if (i < len) K[i] = Kref[i] + Kp[i] - Km[i];
 }
 
+// Approximate diagonalisation (Stewart, Csaszar and Pulay 1982): in the basis of the previous orbitals
+// (occupied i, virtual a; energies eps from the last full eigensolve) the new Fock matrix has a small
+// occupied-virtual block F'_ia; rotating by kappa_ia = F'_ia / (eps_a - eps_i) is the Roothaan step to
+// first order: v_i <- v_i - sum_a kappa_ia v_a, v_a <- v_a + sum_i kappa_ia v_i.
+__global__ void kappa_kernel(double* __restrict__ K, const double* __restrict__ eps, int nocc, int nvir) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nocc * nvir) return;
+    const int i = (int)(idx / nvir), a = (int)(idx % nvir);
+    K[idx] /= fmax(eps[nocc + a] - eps[i], 1e-3);
+}
+
+// P = (15/8) I - (5/4) M + (3/8) M^2: the series of M^{-1/2} about I to second order (M = Q Q^T near I)
+__global__ void invsqrt_series_kernel(double* __restrict__ M, const double* __restrict__ M2, int m) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    M[idx] = (idx / m == idx % m ? 1.875 : 0.0) - 1.25 * M[idx] + 0.375 * M2[idx];
+}
+
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // One molecule's SCF as a sequence of asynchronous iterations with a single host synchronisation each
@@ -299,6 +318,10 @@ class ScfRun {
         DF_CUDA(cudaMalloc((void**)&Fp_, sizeof(double) * nX_ * nX_));
         DF_CUDA(cudaMalloc((void**)&T1_, sizeof(double) * n_ * nX_));
         DF_CUDA(cudaMalloc((void**)&Fo_, sizeof(double) * nX_ * nX_));
+        if (o_.approx_diag) {
+            const long long no = nocc_, nv = nX_ - nocc_;
+            DF_CUDA(cudaMalloc((void**)&abuf_, sizeof(double) * (3 * no * nX_ + no * nv + 2 * no * no)));
+        }
         present_.assign(DIIS_MAX, 0);
         order_.clear();
         h_->history.clear();
@@ -419,18 +442,31 @@ class ScfRun {
         DF_CUDA(cudaMemcpyAsync(d_ints_, pin_ctl_, sizeof(int) * 2 * DIIS_MAX, cudaMemcpyHostToDevice, s_));
         diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, slot_, d_ints_, DIIS_MAX, d_B_);
         DF_CHECK_LAUNCH();
+        // Roothaan step: a full eigensolve, or late (options.approx_diag) a rotation of the previous
+        // orbitals, with a full eigensolve every DIAG_RESET late iterations
+        const bool approx = o_.approx_diag && late_ && fock_basis_ && nX_ > nocc_ && diag_since_full_ >= 0 &&
+                            diag_since_full_ + 1 < DIAG_RESET;
+        double* Fx = approx ? h_->work3.p : Fp_;
         if (it_ >= 2 && order_.size() >= 2) {
             diis_solve_kernel<<<1, 1, 0, s_>>>(d_B_, d_ints_ + DIIS_MAX, (int)order_.size(), d_coef_,
                                                d_ints_ + 2 * DIIS_MAX);
             DF_CHECK_LAUNCH();
             diis_combine_kernel<<<nblk(no), 256, 0, s_>>>(h_->diisF.p, no, d_ints_ + DIIS_MAX, (int)order_.size(),
-                                                         d_coef_, Fp_);
+                                                         d_coef_, Fx);
             DF_CHECK_LAUNCH();
         } else {
             DF_CUDA(cudaMemsetAsync(d_ints_ + 2 * DIIS_MAX, 0, sizeof(int), s_));
-            DF_CUDA(cudaMemcpyAsync(Fp_, Fo_, no * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+            DF_CUDA(cudaMemcpyAsync(Fx, Fo_, no * sizeof(double), cudaMemcpyDeviceToDevice, s_));
         }
-        solve_orth();
+        if (approx) {
+            approx_orth(Fx);
+            ++diag_since_full_;
+            ++r_->approx_steps;
+        } else {
+            solve_orth();
+            if (late_) diag_since_full_ = 0;
+        }
+        last_approx_ = approx;
     }
 
     int status() const { return status_; }
@@ -513,6 +549,44 @@ class ScfRun {
     void solve_orth() {
         eig(Fp_, nX_, h_->eps.p);
         vt_ = Fp_;
+        fock_basis_ = true;
+        occupy();
+    }
+
+    // approximate Roothaan step on the orthogonal-basis Fock matrix Fx: the rows of Fp_ (occupied first)
+    // rotated by kappa, the occupied rows re-orthonormalised by two rounds of the inverse-square-root
+    // series; the virtual rows keep first-order accuracy until the next full eigensolve
+    void approx_orth(const double* Fx) {
+        const int no = nocc_, nv = nX_ - nocc_;
+        double* Vo = Fp_;
+        double* Vv = Fp_ + (long long)no * nX_;
+        double* G = abuf_;                          // no x nX
+        double* Kp = G + (long long)no * nX_;       // no x nv
+        double* VoN = Kp + (long long)no * nv;      // no x nX
+        double* Q = VoN + (long long)no * nX_;      // no x nX
+        double* M = Q + (long long)no * nX_;        // no x no
+        double* M2 = M + (long long)no * no;        // no x no
+        double* VvN = h_->work1.p;                  // nv x nX
+        dgemm(s_, false, false, no, nX_, nX_, 1.0, Vo, nX_, Fx, nX_, 0.0, G, nX_);
+        dgemm(s_, false, true, no, nv, nX_, 1.0, G, nX_, Vv, nX_, 0.0, Kp, nv);    // F'_ia
+        kappa_kernel<<<nblk((long long)no * nv), 256, 0, s_>>>(Kp, h_->eps.p, no, nv);
+        DF_CHECK_LAUNCH();
+        DF_CUDA(cudaMemcpyAsync(VoN, Vo, sizeof(double) * no * nX_, cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaMemcpyAsync(VvN, Vv, sizeof(double) * nv * nX_, cudaMemcpyDeviceToDevice, s_));
+        dgemm(s_, false, false, no, nX_, nv, -1.0, Kp, nv, Vv, nX_, 1.0, VoN, nX_);
+        dgemm(s_, true, false, nv, nX_, no, 1.0, Kp, nv, Vo, nX_, 1.0, VvN, nX_);
+        double *src = VoN, *dst = Q;
+        for (int round = 0; round < 2; ++round) {
+            dgemm(s_, false, true, no, no, nX_, 1.0, src, nX_, src, nX_, 0.0, M, no);
+            dgemm(s_, false, false, no, no, no, 1.0, M, no, M, no, 0.0, M2, no);
+            invsqrt_series_kernel<<<nblk((long long)no * no), 256, 0, s_>>>(M, M2, no);
+            DF_CHECK_LAUNCH();
+            dgemm(s_, false, false, no, nX_, no, 1.0, M, no, src, nX_, 0.0, dst, nX_);
+            std::swap(src, dst);
+        }
+        DF_CUDA(cudaMemcpyAsync(Vo, src, sizeof(double) * no * nX_, cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaMemcpyAsync(Vv, VvN, sizeof(double) * nv * nX_, cudaMemcpyDeviceToDevice, s_));
+        vt_ = Fp_;
         occupy();
     }
 
@@ -531,6 +605,7 @@ class ScfRun {
         dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work2.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
         dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
         eig(Fp_, nX_, h_->eps.p);
+        fock_basis_ = false;
         // ascending eigenvalues: the occupied natural orbitals are the last nocc eigenvectors
         vt_ = Fp_ + (long long)(nX_ - nocc_) * nX_;
         occupy();
@@ -539,7 +614,12 @@ class ScfRun {
 
     void finish() {
         h_->tc_err_host = nullptr;
-        // all orbitals of the last Roothaan step, C = X V
+        // after an approximate step the orbital energies and virtual orbitals are refreshed from the last
+        // Fock matrix; then all orbitals of the last Roothaan step, C = X V
+        if (last_approx_) {
+            DF_CUDA(cudaMemcpyAsync(Fp_, Fo_, sizeof(double) * nX_ * nX_, cudaMemcpyDeviceToDevice, s_));
+            eig(Fp_, nX_, h_->eps.p);
+        }
         if (vt_ == Fp_) dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
         done_ = true;
         r_->converged = (status_ == DF_OK);
@@ -560,6 +640,8 @@ class ScfRun {
         if (Fp_) cudaFree(Fp_);
         if (T1_) cudaFree(T1_);
         if (Fo_) cudaFree(Fo_);
+        if (abuf_) cudaFree(abuf_);
+        abuf_ = nullptr;
         if (Kref_) cudaFree(Kref_);
         if (Cref_) cudaFree(Cref_);
         if (Wq_) cudaFree(Wq_);
@@ -595,6 +677,10 @@ class ScfRun {
     const double* vt_ = nullptr;   // occupied eigenvectors (nocc rows of length nX) of the last Roothaan step
     double *Kref_ = nullptr, *Cref_ = nullptr, *Wq_ = nullptr, *core_ = nullptr;   // incremental Fock state
     bool late_ = false;            // past the max|e| < 1e-4 point (split: the 5-slice builds)
+    double* abuf_ = nullptr;       // approximate diagonalisation scratch
+    bool fock_basis_ = false;      // Fp_ holds eigenvectors of a Fock matrix (eps their energies)
+    bool last_approx_ = false;     // the last Roothaan step was approximate
+    int diag_since_full_ = -1;     // late approximate steps since the last full eigensolve (-1: none yet)
     int inc_since_ref_ = -1;       // density-change builds since the reference (-1: no reference yet)
     double* pin_ = nullptr;
     int* pin_ctl_ = nullptr;
