@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -337,6 +338,15 @@ class ScfRun {
     }
 
     bool done() const { return done_; }
+
+    // the enqueued iteration has completed on the device (errors of the stream are raised)
+    bool ready() const {
+        const cudaError_t e = cudaEventQuery(ev_done_);
+        if (e == cudaSuccess) return true;
+        if (e == cudaErrorNotReady) return false;
+        DF_CUDA(e);
+        return false;
+    }
 
     // J/K, Fock, energy, error vector; scalars and status words copied to pinned memory; one event
     void enqueue_iteration() {
@@ -703,8 +713,10 @@ int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* gue
     return run.status();
 }
 
-// Many molecules in lock-step: each iteration enqueues every unfinished molecule's work on its own
-// stream before waiting on any of them, so kernels of different molecules overlap on the GPU.
+// Many molecules on one host thread, driven by completion events: a molecule whose enqueued iteration
+// has finished on its stream is advanced (convergence test, DIIS, Roothaan step, next iteration) without
+// waiting for the others, and one more molecule is started per pass, so its B build (which waits only
+// on its own stream) runs while the queued iterations of the others proceed on the GPU.
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs) {
     std::vector<std::unique_ptr<ScfRun>> runs;
     for (int i = 0; i < nmol; ++i) {
@@ -713,17 +725,26 @@ int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs
     }
     int status = DF_OK;
     try {
-        for (auto& r : runs) r->begin();
-        bool active = true;
-        while (active) {
-            active = false;
-            for (auto& r : runs)
-                if (!r->done()) r->enqueue_iteration();
-            for (auto& r : runs)
-                if (!r->done()) {
-                    r->finish_iteration();
-                    active = active || !r->done();
-                }
+        int started = 0, finished = 0;
+        while (finished < nmol) {
+            bool progressed = false;
+            for (int i = 0; i < started; ++i) {
+                ScfRun& r = *runs[i];
+                if (r.done() || !r.ready()) continue;
+                r.finish_iteration();
+                if (r.done())
+                    ++finished;
+                else
+                    r.enqueue_iteration();
+                progressed = true;
+            }
+            if (started < nmol) {
+                runs[started]->begin();
+                runs[started]->enqueue_iteration();
+                ++started;
+                progressed = true;
+            }
+            if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
         for (auto& r : runs)
             if (r->status() != DF_OK && status == DF_OK) status = r->status();
