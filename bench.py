@@ -325,7 +325,7 @@ def gpu_arm(args):
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": e2e_s, "unit": "s/iter (DF J+K build, host buffers)",
                 "h2d_bytes_per_step": int(D.nbytes + C.nbytes), "d2h_bytes_per_step": int(Jh.nbytes + Kh.nbytes)},
-        "gpu_launches": args.steps * launches_per_step(prec),
+        "gpu_launches": int(sum(d.get("jk_launches", launches_per_step(prec)) for d in per)),
         "roofline": roofline,
         "kernel_ms": kernel_ms,
         "autotune": autotune,

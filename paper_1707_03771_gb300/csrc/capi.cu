@@ -205,6 +205,7 @@ void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, dou
         exchange_split(h, dC, nocc, slices, dK);
     else
         exchange_fp64(h, nocc, dK);
+    h->timings_ms[16] = 6 + h->exchange_launches;   // J (pack, gamma, coulomb, split sum, unpack), pad C, K
 }
 
 // K alone for m columns of occupied-like coefficients dC (n x m, device), FP64 or split
@@ -551,7 +552,7 @@ int df_set_stream(df_handle* h, void* stream) {
 
 int df_timings(const df_handle* h, double* ms, int count) {
     if (!h || !ms || count < 0) return DF_E_ARG;
-    for (int i = 0; i < count && i < 16; ++i) ms[i] = h->timings_ms[i];
+    for (int i = 0; i < count && i < 20; ++i) ms[i] = h->timings_ms[i];
     return DF_OK;
 }
 

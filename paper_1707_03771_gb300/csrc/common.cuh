@@ -161,7 +161,8 @@ struct df_handle {
     int nX = 0;
     int ndrop = 0;
 
-    double timings_ms[16] = {0};
+    double timings_ms[20] = {0};
+    int exchange_launches = 0;     // kernel launches of the last exchange build
     std::vector<double> history;   // per SCF iteration: iteration, energy, dE, max|e|, slices, J/K ms
     bool sync_timing = true;       // per-kernel event timings (the batch driver turns them off)
     int* tc_err_host = nullptr;    // set by the SCF driver: the tensor-core kernels' timeout flag is copied

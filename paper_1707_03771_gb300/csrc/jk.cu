@@ -183,6 +183,7 @@ void exchange_fp64(df_handle* h, int nocc, double* dK) {
     DF_CUDA(cudaEventCreate(&e1));
     DF_CUDA(cudaEventCreate(&e2));
     DF_CUDA(cudaEventRecord(e0, s));
+    h->exchange_launches = 3;   // Y transform, K contraction, K reduction
     const size_t ny = (size_t)h->naux * pk.np * ldy;   // the FP64 Y is allocated on first FP64 use only
     if (h->Y.n < ny) h->Y.alloc(ny);
     y_transform_fp64(s, h->B.p, pk.row, pk.nt, h->naux, h->Cpad.p, ldy, nocc, h->Y.p);

@@ -724,6 +724,10 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         }
     }
     DF_CUDA(cudaEventRecord(ev[1], s));
+    {
+        const int nyb = (naux + pblk - 1) / pblk;   // split C, per block (slicing,) Y, re-split Y, K, reduce
+        h->exchange_launches = 4 + nyb * (st->blocked ? 2 : 1);
+    }
     const long long nblk = (naux + st->PB - 1) / st->PB;
     const long long ystr = (long long)naux * np * ldy;
     split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
