@@ -195,6 +195,8 @@ void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* 
 
 // split precision (split_k.cu)
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK);
+void gemm_ff(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+             const double* B, int ldb, double beta, double* C, int ldc);
 void split_clear_error(df_handle* h);
 void free_split(df_handle* h);
 

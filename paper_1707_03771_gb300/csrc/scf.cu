@@ -367,8 +367,8 @@ class ScfRun {
         DF_CHECK_LAUNCH();
         // F' = X^T F X; error e = X^T (FDS - SDF) X = 2 (F' P - P F'), P = V_occ V_occ^T, into the next slot
         to_orth(h_->F.p, Fo_);
-        dgemm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
-        dgemm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
+        mm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
+        mm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
         slot_ = 0;
         if ((int)order_.size() < dsize_) {
             while (present_[slot_]) ++slot_;
@@ -484,6 +484,17 @@ class ScfRun {
   private:
     using clk = std::chrono::steady_clock;
 
+    // SCF algebra products: FP64 in FP64 mode; float-float on the FP32 pipes in split mode (~2^-48 per
+    // product, far below the 1e-7 commutator threshold; at convergence the energy is stationary in the
+    // orbitals, so their rounding enters it at second order)
+    void mm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+            const double* B, int ldb, double beta, double* C, int ldc) {
+        if (o_.precision == DF_PREC_SPLIT)
+            gemm_ff(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else
+            dgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+
     // the full build just enqueued becomes the reference: K_ref = K, C_ref = C_occ
     void set_reference() {
         if (!Kref_) {
@@ -521,7 +532,7 @@ class ScfRun {
         DF_SOLVER(cusolverDnDorgqr(h_->solver, n_, m2, m2, W, n_, tau, work_, lwork_, info_));
         eig(core_, m2, lam);
         // V^T (2m x n): row k = sum_j Z[k][j] Q[:, j]; Q column-major n x 2m is the row-major 2m x n Q^T
-        dgemm(s_, false, false, m2, n_, m2, 1.0, core_, m2, W, n_, 0.0, Vt, n_);
+        mm(s_, false, false, m2, n_, m2, 1.0, core_, m2, W, n_, 0.0, Vt, n_);
         split_factors_kernel<<<nblk((long long)n_ * m), 256, 0, s_>>>(Vt, lam, n_, m, Cp, Cm);
         DF_CHECK_LAUNCH();
         const int inc_slices = o_.precision == DF_PREC_SPLIT ? INC_SLICES : 0;
@@ -550,8 +561,8 @@ class ScfRun {
 
     // Fo = X^T Fm X (nX x nX)
     void to_orth(const double* Fm, double* Fo) {
-        dgemm(s_, false, false, n_, nX_, n_, 1.0, Fm, n_, h_->X.p, nX_, 0.0, T1_, nX_);
-        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fo, nX_);
+        mm(s_, false, false, n_, nX_, n_, 1.0, Fm, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        mm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fo, nX_);
     }
 
     // Roothaan step on the orthogonal-basis Fock matrix held in Fp_: eigenvectors in place (row j of the
@@ -577,21 +588,21 @@ class ScfRun {
         double* M = Q + (long long)no * nX_;        // no x no
         double* M2 = M + (long long)no * no;        // no x no
         double* VvN = h_->work1.p;                  // nv x nX
-        dgemm(s_, false, false, no, nX_, nX_, 1.0, Vo, nX_, Fx, nX_, 0.0, G, nX_);
-        dgemm(s_, false, true, no, nv, nX_, 1.0, G, nX_, Vv, nX_, 0.0, Kp, nv);    // F'_ia
+        mm(s_, false, false, no, nX_, nX_, 1.0, Vo, nX_, Fx, nX_, 0.0, G, nX_);
+        mm(s_, false, true, no, nv, nX_, 1.0, G, nX_, Vv, nX_, 0.0, Kp, nv);    // F'_ia
         kappa_kernel<<<nblk((long long)no * nv), 256, 0, s_>>>(Kp, h_->eps.p, no, nv);
         DF_CHECK_LAUNCH();
         DF_CUDA(cudaMemcpyAsync(VoN, Vo, sizeof(double) * no * nX_, cudaMemcpyDeviceToDevice, s_));
         DF_CUDA(cudaMemcpyAsync(VvN, Vv, sizeof(double) * nv * nX_, cudaMemcpyDeviceToDevice, s_));
-        dgemm(s_, false, false, no, nX_, nv, -1.0, Kp, nv, Vv, nX_, 1.0, VoN, nX_);
-        dgemm(s_, true, false, nv, nX_, no, 1.0, Kp, nv, Vo, nX_, 1.0, VvN, nX_);
+        mm(s_, false, false, no, nX_, nv, -1.0, Kp, nv, Vv, nX_, 1.0, VoN, nX_);
+        mm(s_, true, false, nv, nX_, no, 1.0, Kp, nv, Vo, nX_, 1.0, VvN, nX_);
         double *src = VoN, *dst = Q;
         for (int round = 0; round < 2; ++round) {
-            dgemm(s_, false, true, no, no, nX_, 1.0, src, nX_, src, nX_, 0.0, M, no);
-            dgemm(s_, false, false, no, no, no, 1.0, M, no, M, no, 0.0, M2, no);
+            mm(s_, false, true, no, no, nX_, 1.0, src, nX_, src, nX_, 0.0, M, no);
+            mm(s_, false, false, no, no, no, 1.0, M, no, M, no, 0.0, M2, no);
             invsqrt_series_kernel<<<nblk((long long)no * no), 256, 0, s_>>>(M, M2, no);
             DF_CHECK_LAUNCH();
-            dgemm(s_, false, false, no, nX_, no, 1.0, M, no, src, nX_, 0.0, dst, nX_);
+            mm(s_, false, false, no, nX_, no, 1.0, M, no, src, nX_, 0.0, dst, nX_);
             std::swap(src, dst);
         }
         DF_CUDA(cudaMemcpyAsync(Vo, src, sizeof(double) * no * nX_, cudaMemcpyDeviceToDevice, s_));
@@ -602,18 +613,18 @@ class ScfRun {
 
     // dC = C_occ = X V_occ (n x nocc) from the occupied rows vt_ ; D = 2 C_occ C_occ^T
     void occupy() {
-        dgemm(s_, false, true, n_, nocc_, nX_, 1.0, h_->X.p, nX_, vt_, nX_, 0.0, h_->dC.p, nocc_);
-        dgemm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
+        mm(s_, false, true, n_, nocc_, nX_, 1.0, h_->X.p, nX_, vt_, nX_, 0.0, h_->dC.p, nocc_);
+        mm(s_, false, true, n_, n_, nocc_, 2.0, h_->dC.p, nocc_, h_->dC.p, nocc_, 0.0, h_->Dm.p, n_);
     }
 
     // first orbitals from a guess density D0 (host): the nocc eigenvectors of X^T S D0 S X with the
     // largest eigenvalues, C = X V_occ, D = 2 C C^T
     void natural_orbitals(const double* D0) {
         DF_CUDA(cudaMemcpyAsync(h_->work3.p, D0, nn_ * sizeof(double), cudaMemcpyHostToDevice, s_));
-        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->S.p, n_, h_->work3.p, n_, 0.0, h_->work1.p, n_);
-        dgemm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
-        dgemm(s_, false, false, n_, nX_, n_, 1.0, h_->work2.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
-        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
+        mm(s_, false, false, n_, n_, n_, 1.0, h_->S.p, n_, h_->work3.p, n_, 0.0, h_->work1.p, n_);
+        mm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
+        mm(s_, false, false, n_, nX_, n_, 1.0, h_->work2.p, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        mm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fp_, nX_);
         eig(Fp_, nX_, h_->eps.p);
         fock_basis_ = false;
         // ascending eigenvalues: the occupied natural orbitals are the last nocc eigenvectors
@@ -630,7 +641,7 @@ class ScfRun {
             DF_CUDA(cudaMemcpyAsync(Fp_, Fo_, sizeof(double) * nX_ * nX_, cudaMemcpyDeviceToDevice, s_));
             eig(Fp_, nX_, h_->eps.p);
         }
-        if (vt_ == Fp_) dgemm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
+        if (vt_ == Fp_) mm(s_, false, true, n_, nX_, nX_, 1.0, h_->X.p, nX_, Fp_, nX_, 0.0, h_->C.p, nX_);
         done_ = true;
         r_->converged = (status_ == DF_OK);
         r_->status = status_;
