@@ -331,6 +331,7 @@ def gpu_arm(args):
         "autotune": autotune,
         "compare": compare,
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
+                    "potrf_ms": build_ms.get("potrf_ms"), "trtri_ms": build_ms.get("trtri_ms"),
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
                     "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
         "time_to_converge_s": ttc or None, "scf": scf_info or None, "dE_split_vs_fp64": de_iter,

@@ -247,7 +247,7 @@ class Handle:
         load().df_timings(self.h, _dp(out), 20)
         keys = ["init_ms", "eri3c_ms", "cholesky_ms", "whiten_ms", "gamma_ms", "coulomb_ms", "ytransform_ms",
                 "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms", "split_other_ms", "tc_y_tile_n",
-                "tc_k_split", "autotune_ms", "tc_k_tile_n", "jk_launches"]
+                "tc_k_split", "autotune_ms", "tc_k_tile_n", "jk_launches", "potrf_ms", "trtri_ms"]
         return dict(zip(keys, out[:len(keys)]))
 
     def close(self):

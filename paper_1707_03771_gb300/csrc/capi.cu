@@ -114,6 +114,44 @@ int fail(df_handle* h, const Error& e) {
 
 }  // namespace
 
+// Inverse of a lower-triangular block of at most 64 rows in place (row-major, leading dimension ld): the
+// block is read into shared memory, then one thread per column j forward-substitutes and writes column j
+// of the inverse (it reads back only values it wrote itself).
+__global__ void tri_inv_small_kernel(double* __restrict__ L, int m, long long ld) {
+    __shared__ double a[64][65];
+    const int j = threadIdx.x;
+    for (int r = 0; r < m; ++r)
+        if (j < m) a[r][j] = L[(long long)r * ld + j];
+    __syncthreads();
+    if (j >= m) return;
+    for (int i = 0; i < j; ++i) L[(long long)i * ld + j] = 0.0;
+    L[(long long)j * ld + j] = 1.0 / a[j][j];
+    for (int i = j + 1; i < m; ++i) {
+        double t = 0.0;
+        for (int k = j; k < i; ++k) t = fma(a[i][k], L[(long long)k * ld + j], t);
+        L[(long long)i * ld + j] = -t / a[i][i];
+    }
+}
+
+// L^-1 in place for lower-triangular L (m x m inside a row-major array of leading dimension ld; the
+// upper triangle zero): with L = [[L11, 0], [L21, L22]], L^-1 = [[L11^-1, 0], [-L22^-1 L21 L11^-1, L22^-1]]
+// by recursion, the off-diagonal block by two FP64 products (T is m/2 x m/2 scratch).
+void tri_inv_lower(cudaStream_t s, double* L, int m, long long ld, double* T) {
+    if (m <= 64) {
+        tri_inv_small_kernel<<<1, 64, 0, s>>>(L, m, ld);
+        DF_CHECK_LAUNCH();
+        return;
+    }
+    const int m1 = ((m / 2 + 63) / 64) * 64, m2 = m - m1;
+    double* L11 = L;
+    double* L21 = L + (long long)m1 * ld;
+    double* L22 = L21 + m1;
+    tri_inv_lower(s, L11, m1, ld, T);
+    tri_inv_lower(s, L22, m2, ld, T);
+    dgemm(s, false, false, m2, m1, m1, 1.0, L21, (int)ld, L11, (int)ld, 0.0, T, m1);     // L21 L11^-1
+    dgemm(s, false, false, m2, m1, m2, -1.0, L22, (int)ld, T, m1, 0.0, L21, (int)ld);   // -L22^-1 (L21 L11^-1)
+}
+
 void build_B(df_handle* h, double tau, bool keep) {
     cudaStream_t s = h->stream;
     const size_t rows = (size_t)h->naux * h->pk.row;
@@ -126,7 +164,7 @@ void build_B(df_handle* h, double tau, bool keep) {
     compute_three_center(h, h->A3c.p, tau);
     DF_CUDA(cudaEventRecord(ev[1], s));
     // metric Cholesky (P|Q) = L L^T: cuSOLVER works column-major, so the upper factor U (V = U^T U)
-    // of the column-major matrix is the row-major lower factor L = U^T; likewise trtri of U gives L^-1.
+    // of the column-major matrix is the row-major lower factor L = U^T (trtri of U would give L^-1).
     const int na = h->naux;
     h->Linv.alloc((size_t)na * na);
     DF_CUDA(cudaMemcpyAsync(h->Linv.p, h->metric.p, sizeof(double) * na * na, cudaMemcpyDeviceToDevice, s));
@@ -138,22 +176,39 @@ void build_B(df_handle* h, double tau, bool keep) {
     DF_CUDA(cudaMalloc((void**)&info, sizeof(int)));
     int hinfo = 0;
     try {
+        const auto tp0 = std::chrono::steady_clock::now();
         DF_SOLVER(cusolverDnDpotrf(h->solver, CUBLAS_FILL_MODE_UPPER, na, h->Linv.p, na, work, lwork, info));
         DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
         DF_CUDA(cudaStreamSynchronize(s));
         if (hinfo != 0) throw Error{DF_E_NUMERIC, "metric (P|Q) is not positive definite (potrf info " + std::to_string(hinfo) + ")"};
-        size_t dws = 0, hws = 0;
-        DF_SOLVER(cusolverDnXtrtri_bufferSize(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
-                                              h->Linv.p, na, &dws, &hws));
-        void* dbuf = nullptr;
-        std::vector<char> hbuf(std::max<size_t>(hws, 1));
-        DF_CUDA(cudaMalloc(&dbuf, std::max<size_t>(dws, 1)));
-        cusolverStatus_t st = cusolverDnXtrtri(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
-                                               h->Linv.p, na, dbuf, dws, hbuf.data(), hws, info);
-        DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-        DF_CUDA(cudaStreamSynchronize(s));
-        cudaFree(dbuf);
-        if (st != CUSOLVER_STATUS_SUCCESS) throw Error{DF_E_CUDA, "cusolverDnXtrtri failed"};
+        const auto tp1 = std::chrono::steady_clock::now();
+        h->timings_ms[17] = std::chrono::duration<double, std::milli>(tp1 - tp0).count();   // potrf
+        // the factor's inverse by blocks (FP64 products); DFHF_TRTRI=cusolver selects cuSOLVER's trtri, whose
+        // first call in a process was measured at up to 0.9 s (4384 functions) against 0.08-0.14 s here
+        const char* tri = std::getenv("DFHF_TRTRI");
+        if (!(tri && std::string(tri) == "cusolver")) {
+            // the row-major lower factor: zero its upper triangle, then invert by blocks
+            zero_upper_kernel<<<(unsigned)(((long long)na * na + 255) / 256), 256, 0, s>>>(h->Linv.p, na);
+            DF_CHECK_LAUNCH();
+            DevBuf<double> T;
+            T.alloc((size_t)((na / 2 + 63) / 64 * 64) * (size_t)(na / 2 + 64));
+            tri_inv_lower(s, h->Linv.p, na, na, T.p);
+            DF_CUDA(cudaStreamSynchronize(s));
+        } else {
+            size_t dws = 0, hws = 0;
+            DF_SOLVER(cusolverDnXtrtri_bufferSize(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
+                                                  h->Linv.p, na, &dws, &hws));
+            void* dbuf = nullptr;
+            std::vector<char> hbuf(std::max<size_t>(hws, 1));
+            DF_CUDA(cudaMalloc(&dbuf, std::max<size_t>(dws, 1)));
+            cusolverStatus_t st = cusolverDnXtrtri(h->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, na, CUDA_R_64F,
+                                                   h->Linv.p, na, dbuf, dws, hbuf.data(), hws, info);
+            DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+            DF_CUDA(cudaStreamSynchronize(s));
+            cudaFree(dbuf);
+            if (st != CUSOLVER_STATUS_SUCCESS) throw Error{DF_E_CUDA, "cusolverDnXtrtri failed"};
+        }
+        h->timings_ms[18] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp1).count();
         if (hinfo != 0) throw Error{DF_E_NUMERIC, "metric Cholesky factor is singular"};
     } catch (...) {
         cudaFree(work);

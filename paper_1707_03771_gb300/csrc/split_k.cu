@@ -494,6 +494,7 @@ struct SplitState {
     int2* tiles128 = nullptr;    // lower 128-tile pairs
     float2* Kpart_tc = nullptr;  // [nsplit_tc][npt][npt]
     int npt = 0, ntiles128 = 0, nsplit_tc = 0, kcap = 0;   // kcap: splits Kpart_tc has room for
+    int ksplit_heur = 1;         // K split of the occupancy heuristic (about 4 CTAs per SM)
     int yN = 80;                 // tile width of the tensor-core Y kernel
     int kN = 64;                 // half-tile width of the tensor-core K kernel
     int S = 0;
@@ -570,11 +571,11 @@ void prepare_b(df_handle* h, SplitState* st) {
 }
 
 // ---- autotuner ----------------------------------------------------------------------------------
-// The tile width of the tensor-core Y kernel (32, 64 or 80 columns dividing ldy), and the tile width (32
-// or 64) and auxiliary-block split of the K kernel, are picked by timing the candidates on the call's own
-// operands the first time a size bucket (np, ldy, naux / 512, S) is met; the choice is kept for the
-// process. Y is timed on the first auxiliary block (all rows when every slice is resident), K on the
-// finished Y slices; every candidate computes the same values.
+// The tile width of the tensor-core Y kernel (32, 64 or 80 columns dividing ldy) and of the K kernel (32
+// or 64) are picked by timing the candidates on the call's own operands the first time a size bucket
+// (np, ldy, naux / 512, S) is met; the choice is kept for the process. Y is timed on the first auxiliary
+// block (all rows when every slice is resident), K on the finished Y slices. Every width computes the
+// same values bit for bit; the K split over auxiliary blocks comes from the occupancy heuristic.
 struct TcChoice {
     int yN = 0, kN = 64, ksplit = 0;
 };
@@ -620,26 +621,19 @@ void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
     cudaStream_t s = h->stream;
     const int np = st->np, ldy = st->ldy, naux = h->naux;
     const long long nblk = (naux + st->PB - 1) / st->PB;
-    const int h0 = std::max(1, (int)std::min<long long>(st->nsplit_tc, nblk));   // occupancy heuristic
-    std::vector<int> cands;
-    for (int c : {1, std::max(1, h0 / 2), h0, 2 * h0, 4 * h0}) {
-        const long long bytes = (long long)c * st->npt * st->npt * sizeof(float2);
-        if (c <= nblk && bytes <= (2LL << 30) && std::find(cands.begin(), cands.end(), c) == cands.end())
-            cands.push_back(c);
-    }
-    const int cmax = *std::max_element(cands.begin(), cands.end());
-    if (cmax > st->kcap) {
+    const int h0 = std::max(1, (int)std::min<long long>(st->ksplit_heur, nblk));   // occupancy heuristic
+    if (h0 > st->kcap) {
         DF_CUDA(cudaStreamSynchronize(s));
         cudaFree(st->Kpart_tc);
         st->Kpart_tc = nullptr;
-        DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * cmax * (long long)st->npt * st->npt));
-        st->kcap = cmax;
+        DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * h0 * (long long)st->npt * st->npt));
+        st->kcap = h0;
     }
-    // the half-tile width at the heuristic's split, then the split at that width
+    // the half-tile width at the heuristic's split
     double best_ms = 1e30;
     for (int N : {64, 32}) {
         const double ms = time_once(s, [&] {
-            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, std::min(h0, cmax), st->tiles128, st->ntiles128,
+            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, h0, st->tiles128, st->ntiles128,
                        st->Kpart_tc, st->npt, st->err);
         });
         if (ms < best_ms) {
@@ -647,17 +641,9 @@ void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
             best.kN = N;
         }
     }
-    best_ms = 1e30;
-    for (int c : cands) {
-        const double ms = time_once(s, [&] {
-            k_split_tc(s, S, best.kN, st->Ys, st->Ye, naux, np, ldy, st->PB, c, st->tiles128, st->ntiles128,
-                       st->Kpart_tc, st->npt, st->err);
-        });
-        if (ms < best_ms) {
-            best_ms = ms;
-            best.ksplit = c;
-        }
-    }
+    // the split changes how the float-float partial sums are grouped (hence the last bits of K), so it
+    // is not chosen by timing: the occupancy heuristic keeps results identical from run to run
+    best.ksplit = h0;
 }
 
 // Y over auxiliary blocks: one block of all rows when every slice is resident; otherwise the slices of
@@ -743,7 +729,10 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         }
         // a choice made for another handle of the bucket: at most one split per auxiliary block, and room
         // for it in the partial-sum buffer
-        const int ksplit = (int)std::min<long long>(ch.ksplit, nblk);
+        // the override's split, else this state's own heuristic (a cached choice carries only widths)
+        const int ksplit = (int)std::min<long long>(std::getenv("DFHF_TC_TILES") && ch.ksplit > 0 ? ch.ksplit
+                                                                                                 : st->ksplit_heur,
+                                                    nblk);
         st->ch_y[S] = ch.yN;
         st->ch_k[S] = ch.kN;
         st->ch_split[S] = ksplit;
@@ -875,6 +864,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         DF_CUDA(cudaMalloc((void**)&st->tiles128, sizeof(int2) * t128.size()));
         DF_CUDA(cudaMemcpy(st->tiles128, t128.data(), sizeof(int2) * t128.size(), cudaMemcpyHostToDevice));
         st->nsplit_tc = std::max(1, std::min((4 * 152 + 2 * st->ntiles128 - 1) / (2 * st->ntiles128), (int)nblk));
+        st->ksplit_heur = st->nsplit_tc;
         cudaFree(st->Kpart_tc);
         st->Kpart_tc = nullptr;
         DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * st->nsplit_tc * (long long)st->npt * st->npt));
