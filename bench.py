@@ -257,10 +257,6 @@ def gpu_arm(args):
         de_iter = {"per_iteration": [float(f"{x:.3e}") for x in (a[:m] - b[:m])],
                    "at_convergence": float(scf_info["split"]["energy"] - scf_info["fp64"]["energy"])}
 
-    batched = None
-    if args.batch > 0:
-        batched = batched_measure(binding, clusters, args.batch, torch, rank, dev, args.batch_max_waters)
-
     peaks, peak_src = _peaks()
     keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
             "split_other_ms"]
@@ -303,6 +299,30 @@ def gpu_arm(args):
                     "y_split_tflops": y_tf, "k_split_tflops": k_tf,
                     "fp64_equivalent_tflops": alg_k_flops / ((avg["split_y_ms"] + avg["split_k_ms"] + avg["split_other_ms"]) * 1e-3) / 1e12}
     kernel_ms = {k: round(v, 3) for k, v in avg.items()}
+    # the other rows' rooflines: DF-J reads packed B twice (gamma, coulomb) against HBM; the integral
+    # kernels write packed (P|mu nu) once (FP64 ALU bound); whitening counts naux^2 * npair FP64-equivalent
+    # flops (run as 7-slice BF16 products on the tensor cores unless the float-float form is selected)
+    b_bytes = naux * h.packed_row * 8.0
+    npair = n * (n + 1) // 2
+    hbm = peaks.get("hbm_gbs")
+    j_gbs = 2.0 * b_bytes / ((avg["gamma_ms"] + avg["coulomb_ms"]) * 1e-3) / 1e9
+    eri_s = build_ms["eri3c_ms"] * 1e-3
+    n_triples = int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)
+    wh_s = build_ms["whiten_ms"] * 1e-3
+    other_rooflines = {
+        "df_j": {"kernels": "gamma_kernel + coulomb_kernel (FP64)", "bound": "hbm",
+                 "algorithmic_bytes": 2.0 * b_bytes, "achieved": j_gbs, "peak": hbm, "unit": "GB/s",
+                 "frac": j_gbs / hbm if hbm else None, "peak_source": f"{peak_src} hbm_gbs"},
+        "eri3c": {"kernels": "eri3c_kernel (FP64 Rys)", "bound": "alu",
+                  "shell_triples": n_triples, "gtriples_per_s": n_triples / eri_s / 1e9,
+                  "write_bytes": naux * npair * 8.0, "write_gbs": naux * npair * 8.0 / eri_s / 1e9,
+                  "write_frac_of_hbm": naux * npair * 8.0 / eri_s / 1e9 / hbm if hbm else None},
+        "whitening": {"kernels": "ozaki_tc_kernel<W> (tcgen05 BF16, 7 slices)"
+                      if os.environ.get("DFHF_WHITEN", "tc") != "ff" else "float-float mma.sync",
+                      "fp64_equivalent_flops": float(naux) * naux * npair,
+                      "fp64_equivalent_tflops": float(naux) * naux * npair / wh_s / 1e12,
+                      "vs_fp64_peak": float(naux) * naux * npair / wh_s / 1e12 / FP64_PEAK_TFLOPS},
+    }
     tuned = per[-1]
     autotune = {"y_tile_n": int(tuned.get("tc_y_tile_n", 0)), "k_tile_n": int(tuned.get("tc_k_tile_n", 0)),
                 "k_split": int(tuned.get("tc_k_split", 0)),
@@ -327,20 +347,24 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": int(D.nbytes + C.nbytes), "d2h_bytes_per_step": int(Jh.nbytes + Kh.nbytes)},
         "gpu_launches": int(sum(d.get("jk_launches", launches_per_step(prec)) for d in per)),
         "roofline": roofline,
+        "other_rooflines": other_rooflines,
         "kernel_ms": kernel_ms,
         "autotune": autotune,
         "compare": compare,
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
                     "potrf_ms": build_ms.get("potrf_ms"), "trtri_ms": build_ms.get("trtri_ms"),
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
-                    "eri_triples": int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)},
+                    "eri_triples": n_triples},
         "time_to_converge_s": ttc or None, "scf": scf_info or None, "dE_split_vs_fp64": de_iter,
-        "batched": batched,
+        "batched": None,
         "learned_guess": learned,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
     h.close()
+    # many small clusters, after the large cluster's tensors have left the device
+    if args.batch > 0:
+        line["batched"] = batched_measure(binding, clusters, args.batch, torch, rank, dev, args.batch_max_waters)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -423,6 +447,54 @@ def guess_study(args):
                       "iterations_saved_fraction": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
                       "max_abs_dE_learned_vs_core": float(max(abs(r["dE_learned_vs_core"]) for r in rows)),
                       "all_converged": all(r["converged"] for r in rows), "clusters": rows}))
+
+
+def _oracle_scf_child(name):
+    """The oracle's whole DF-RHF (integrals, whitening, SCF) on one workload; prints one JSON line."""
+    from oracle import dfrhf
+    from paper_1707_03771_gb300 import clusters
+    s = clusters.workload(name)
+    dfrhf.build()
+    t0 = time.perf_counter()
+    r = dfrhf.scf(s)
+    print(json.dumps({"t_s": time.perf_counter() - t0, "energy": r.energy, "iterations": r.iterations}))
+
+
+def oracle_scf_study(args):
+    """Whole SCF runs beside the oracle on the same host: for each workload, the GPU FP64 and split-precision
+    SCF (B built and timed) and the oracle's DF-RHF on all host cores, and on one core for workloads of at
+    most 100 basis functions. The oracle runs in child processes. Prints one JSON line."""
+    import torch
+    from paper_1707_03771_gb300 import binding, build, clusters
+    build.build()
+    binding.load()
+    rows = []
+    for name in args.oracle_scf.split(","):
+        s = clusters.workload(name)
+        row = {"workload": name, "n": s.nbf, "naux": s.naux, "nocc": s.nocc}
+        with binding.Handle(s) as h:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.build_B()
+            torch.cuda.synchronize()
+            t_build = time.perf_counter() - t0
+            for label, p, inc in (("gpu_fp64", binding.DF_PREC_FP64, 0), ("gpu_split", binding.DF_PREC_SPLIT, 1)):
+                r = h.scf(precision=p, slices=3, incremental=inc, approx_diag=inc)
+                row[label] = {"t_s": t_build + r["t_total_s"], "energy": r["energy"],
+                              "iterations": r["iterations"], "converged": bool(r["converged"])}
+        threads = [("oracle", os.cpu_count())] + ([("oracle_1_thread", 1)] if s.nbf <= 100 else [])
+        for label, nt in threads:
+            env = dict(os.environ)
+            if nt == 1:
+                env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-scf-child", name],
+                                 env=env, capture_output=True, text=True, check=True)
+            row[label] = dict(json.loads(out.stdout.strip().splitlines()[-1]), cores=nt)
+        row["dE_gpu_fp64_vs_oracle"] = row["gpu_fp64"]["energy"] - row["oracle"]["energy"]
+        row["dE_gpu_split_vs_oracle"] = row["gpu_split"]["energy"] - row["oracle"]["energy"]
+        rows.append(row)
+    print(json.dumps({"study": "whole SCF: GPU (build B + SCF) beside the oracle on the host cores",
+                      "workloads": rows}))
 
 
 def batched_measure(binding, clusters, count, torch, rank=0, dev=None, wmax=8):
@@ -543,10 +615,17 @@ def main():
     ap.add_argument("--learned", type=int, default=32, help="training clusters for the learned guess (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--oracle-scf", default=None, metavar="WORKLOADS",
+                    help="only whole SCF runs, GPU beside the oracle, e.g. water2,water8 (one JSON line)")
+    ap.add_argument("--oracle-scf-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.guess_study:
+    if args.oracle_scf_child:
+        _oracle_scf_child(args.oracle_scf_child)
+    elif args.oracle_scf:
+        oracle_scf_study(args)
+    elif args.guess_study:
         guess_study(args)
     elif args.impl == "reference":
         reference_arm(args)
