@@ -6,6 +6,17 @@
 
 namespace dfhf {
 
+// Longest exact chunk of a product of S-slice operands, in contraction terms (a multiple of 64). The pairs
+// (s, t) with s + t = L + 2 meet in level L; per term the top level S - 1 is the largest, at most
+// 2 * 128 * 64 (d_1 with d_S, twice) + (S - 2) * 64 * 64 (the inner pairs) = 2^14 + (S - 2) 2^12. A chunk
+// of K terms keeps every level sum an integer of magnitude <= K * that <= 2^24, exact in FP32 whatever
+// the order of the tensor-core additions: 1024, 768, 640, 576 and 448 terms for S = 2, 3, 4, 5 and 7.
+template <int S>
+constexpr int exact_chunk() {
+    return ((1 << 24) / ((1 << 14) + (S > 2 ? S - 2 : 0) * (1 << 12))) / 64 * 64;
+}
+static_assert(exact_chunk<3>() == 768 && exact_chunk<5>() == 576 && exact_chunk<7>() == 448, "exact chunks");
+
 // 2^e as a double, -1022 <= e <= 1023
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 

@@ -37,7 +37,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int KT = 32;             // contraction tile (elements)
 constexpr int LDS = KT + 8;        // padded shared-memory row (bf16): 80 B, conflict-free ldmatrix
-constexpr int CHUNK_TILES = 16;    // 512-element exact chunks
+constexpr int CHUNK_TILES = 16;    // exchange chunks: whole auxiliary rows, at most 512 elements (exact for S <= 5)
 constexpr int SMAX = 5;
 
 // exact 2^e as a float; 0 below the normal range (such contributions are below 2^-126 of the scale)
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(320) y_split_kernel(const bf16* __restrict__ B
         __syncthreads();
         if (wn * WNT < b_rows) mma_tile<S>(f, sA + cur * S * 64 * LDS, 64, sB + cur * S * BN * LDS, BN, wm, wn, lane);
         __syncthreads();
-        if ((kt + 1) % CHUNK_TILES == 0 || kt + 1 == nk) drain<S>(f, sEa + wm * 32, sEb + wn * WNT, lane);
+        if ((kt + 1) % (exact_chunk<S>() / KT) == 0 || kt + 1 == nk) drain<S>(f, sEa + wm * 32, sEb + wn * WNT, lane);
     }
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll

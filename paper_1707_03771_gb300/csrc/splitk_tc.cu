@@ -37,8 +37,11 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TM = 128;            // output rows per CTA (TMEM lanes)
 constexpr int KS = 64;             // K elements per pipeline step (one 128-byte swizzle row)
-constexpr int CHUNK_STEPS = 8;     // 512-element exact chunks (S <= 5)
-constexpr int CHUNK_STEPS_W = 7;   // 448-element exact chunks (whitening, S = 7)
+// pipeline steps per exact chunk: 12 (S = 3), 9 (S = 5), 7 (whitening, S = 7)
+template <int S>
+constexpr int chunk_steps() {
+    return exact_chunk<S>() / KS;
+}
 // A-slice ring slots (one 128 x 64 slice each): 4, or 3 where that lets two CTAs share an SM
 template <int S, int N>
 constexpr int ring_slots() {
@@ -251,9 +254,9 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     fence_after();
     const unsigned tmem = *tmem_slot;
 
-    // chunk index of K-step ks (MODE 0: 8 steps; MODE 1: PB auxiliary rows; MODE 2: 7 steps)
+    // chunk index of K-step ks (MODE 0 and 2: the exact chunk of S slices; MODE 1: PB auxiliary rows)
     auto chunk_of = [&](int ks) {
-        return MODE == 0 ? ks / CHUNK_STEPS : (MODE == 2 ? ks / CHUNK_STEPS_W : (ks / kpp) / args.PB);
+        return MODE == 1 ? (ks / kpp) / args.PB : ks / chunk_steps<S>();
     };
     const int nchunks = ksteps > 0 ? chunk_of(ksteps - 1) + 1 : 0;
 
