@@ -133,9 +133,43 @@ __global__ void tri_inv_small_kernel(double* __restrict__ L, int m, long long ld
     }
 }
 
+// Z <- L^-1 Z for a lower-triangular block of at most 64 rows (row-major, leading dimension ld) and the
+// m x ncol right-hand sides Z (leading dimension ldz): one thread per column, forward substitution.
+__global__ void tri_solve_small_kernel(const double* __restrict__ L, int m, long long ld, double* __restrict__ Z,
+                                       int ncol, long long ldz) {
+    __shared__ double a[64][65];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) a[e / m][e % m] = L[(long long)(e / m) * ld + e % m];
+    __syncthreads();
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncol) return;
+    for (int i = 0; i < m; ++i) {
+        double t = Z[(long long)i * ldz + j];
+        for (int k = 0; k < i; ++k) t = fma(-a[i][k], Z[(long long)k * ldz + j], t);
+        Z[(long long)i * ldz + j] = t / a[i][i];
+    }
+}
+
+// Z <- L^-1 Z (L lower triangular m x m, leading dimension ld; Z m x ncol, leading dimension ldz) by
+// recursion: Z1 <- L11^-1 Z1, Z2 <- Z2 - L21 Z1, Z2 <- L22^-1 Z2 (blocked forward substitution).
+void tri_solve_lower(cudaStream_t s, const double* L, int m, long long ld, double* Z, int ncol, long long ldz) {
+    if (m <= 64) {
+        tri_solve_small_kernel<<<(ncol + 127) / 128, 128, 0, s>>>(L, m, ld, Z, ncol, ldz);
+        DF_CHECK_LAUNCH();
+        return;
+    }
+    const int m1 = ((m / 2 + 63) / 64) * 64, m2 = m - m1;
+    tri_solve_lower(s, L, m1, ld, Z, ncol, ldz);
+    dgemm(s, false, false, m2, ncol, m1, -1.0, L + (long long)m1 * ld, (int)ld, Z, (int)ldz, 1.0,
+          Z + (long long)m1 * ldz, (int)ldz);
+    tri_solve_lower(s, L + (long long)m1 * ld + m1, m2, ld, Z + (long long)m1 * ldz, ncol, ldz);
+}
+
 // L^-1 in place for lower-triangular L (m x m inside a row-major array of leading dimension ld; the
-// upper triangle zero): with L = [[L11, 0], [L21, L22]], L^-1 = [[L11^-1, 0], [-L22^-1 L21 L11^-1, L22^-1]]
-// by recursion, the off-diagonal block by two FP64 products (T is m/2 x m/2 scratch).
+// upper triangle zero): with L = [[L11, 0], [L21, L22]], L^-1 = [[L11^-1, 0], [X21, L22^-1]] by recursion.
+// X21 = -L22^-1 (L21 L11^-1) is taken by forward substitution with L22 before L22 is inverted: multiplying
+// by the explicit L22^-1 instead left residuals |X L - I| a hundred times larger on an ill-conditioned
+// metric (condition number 5e11 at 8 waters), enough to move the SCF energy by 1e-6 Eh. T is scratch
+// of (m/2 + 64) x (m/2 + 64) doubles.
 void tri_inv_lower(cudaStream_t s, double* L, int m, long long ld, double* T) {
     if (m <= 64) {
         tri_inv_small_kernel<<<1, 64, 0, s>>>(L, m, ld);
@@ -147,9 +181,11 @@ void tri_inv_lower(cudaStream_t s, double* L, int m, long long ld, double* T) {
     double* L21 = L + (long long)m1 * ld;
     double* L22 = L21 + m1;
     tri_inv_lower(s, L11, m1, ld, T);
+    dgemm(s, false, false, m2, m1, m1, -1.0, L21, (int)ld, L11, (int)ld, 0.0, T, m1);    // -L21 L11^-1
+    tri_solve_lower(s, L22, m2, ld, T, m1, m1);                                         // X21 = L22^-1 T
+    DF_CUDA(cudaMemcpy2DAsync(L21, sizeof(double) * ld, T, sizeof(double) * m1, sizeof(double) * m1, m2,
+                              cudaMemcpyDeviceToDevice, s));
     tri_inv_lower(s, L22, m2, ld, T);
-    dgemm(s, false, false, m2, m1, m1, 1.0, L21, (int)ld, L11, (int)ld, 0.0, T, m1);     // L21 L11^-1
-    dgemm(s, false, false, m2, m1, m2, -1.0, L22, (int)ld, T, m1, 0.0, L21, (int)ld);   // -L22^-1 (L21 L11^-1)
 }
 
 void build_B(df_handle* h, double tau, bool keep) {
@@ -176,6 +212,7 @@ void build_B(df_handle* h, double tau, bool keep) {
     DF_CUDA(cudaMalloc((void**)&info, sizeof(int)));
     int hinfo = 0;
     try {
+        DF_CUDA(cudaStreamSynchronize(s));   // the integral kernels ahead on the stream are not potrf's time
         const auto tp0 = std::chrono::steady_clock::now();
         DF_SOLVER(cusolverDnDpotrf(h->solver, CUBLAS_FILL_MODE_UPPER, na, h->Linv.p, na, work, lwork, info));
         DF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
