@@ -124,7 +124,7 @@ def _peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel and tile on the same workload;
 # keyed by (workload, kernel, slices, tile width). Anything not captured reports null.
-NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.57e9 + 8.97e9, ("water32", "K", 5, 32): 73.31e9 + 0.04e9}
+NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.588e9 + 8.975e9, ("water32", "K", 5, 32): 72.219e9 + 0.044e9}
 
 # FP64 DFMA peak of GB300 measured with a dependent-chain-free DFMA loop over all 152 SMs
 # (1.00 TFLOP/s; DMMA m8n8k4 gave 1.05 TFLOP/s).
