@@ -203,6 +203,13 @@ int df_get_matrix(df_handle* h, int which, double* out);
  * by Rys quadrature). A test hook for the device routine the integral kernels use. 1 <= nroots <= 4. */
 int df_rys(const double* T, int count, int nroots, double* x, double* w);
 
+/* rint(v[i] 2^k[i]) with ties to even, for `count` values (host arrays; runs on the host, no GPU needed):
+ * the integer T from which the split-precision kernels peel the BF16 slices of a value whose row has the
+ * power of two e (k = 7 S - e; Ozaki, Ogita, Oishi and Rump's error-free splitting, the reading of the
+ * paper's silent precision point). A test hook for the device routine, which takes the same code.
+ * Returns DF_E_ARG for a negative count or a null array. */
+int df_rint_pow2(const double* v, const int* k, long long count, long long* out);
+
 /* Coulomb matrix J (n x n, device pointer) for the density D (n x n, device pointer) without any
  * device allocation; the paper has no counterpart. For callers that cannot call cudaMalloc (a host
  * application that owns all device memory through its own allocator, or a latency-critical loop that

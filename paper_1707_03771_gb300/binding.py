@@ -19,7 +19,7 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_row
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
             "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
-            "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess"]
+            "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2"]
 DF_MLP_NFEAT = 57
 
 
@@ -77,6 +77,7 @@ def load(path: str | None = None):
     L.df_get_rows.argtypes = [c_void_p, c_int, c_int, c_int, dp]
     L.df_get_matrix.argtypes = [c_void_p, c_int, dp]
     L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
+    L.df_rint_pow2.argtypes = [dp, P(c_int), ctypes.c_longlong, P(ctypes.c_longlong)]
     L.df_prepare.argtypes = []
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
@@ -401,6 +402,18 @@ def scf_waves(systems, budget_bytes, precision=DF_PREC_FP64, slices=3, **kw):
         for k, r in zip(wave, res):
             results[k] = r
     return results
+
+
+def rint_pow2(v, k):
+    """rint(v 2^k), ties to even, by the library's splitting routine run on the host (test hook)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    k = np.ascontiguousarray(np.broadcast_to(k, v.shape), dtype=np.int32)
+    out = np.empty(v.shape, dtype=np.int64)
+    rc = load().df_rint_pow2(_dp(v), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), v.size,
+                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    if rc != DF_OK:
+        raise DFError(rc, "df_rint_pow2")
+    return out
 
 
 def rys(T, nroots):

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace dfhf {
 
@@ -595,6 +596,12 @@ int df_get_matrix(df_handle* h, int which, double* out) {
     } catch (const Error& e) {
         return fail(h, e);
     }
+    return DF_OK;
+}
+
+int df_rint_pow2(const double* v, const int* k, long long count, long long* out) {
+    if (count < 0 || (count > 0 && (!v || !k || !out))) return DF_E_ARG;
+    for (long long i = 0; i < count; ++i) out[i] = dfhf::rint_pow2(v[i], k[i]);
     return DF_OK;
 }
 
