@@ -95,10 +95,11 @@ def test_tile_widths_give_identical_exchange(lib, slices):
         assert np.array_equal(v, ref), k
 
 
-def test_blocked_slices_match_resident_slices(lib):
+@pytest.mark.parametrize("rows", ["100", "1"])
+def test_blocked_slices_match_resident_slices(lib, rows):
     """When B's slices do not fit in HBM they are cut per block of auxiliary rows at every build; at 5
-    slices the digits are the same as with every row resident, so K is bitwise identical (ragged last
-    block: 1096 rows in blocks of 100)."""
+    slices the digits are the same as with every row resident, so K is bitwise identical. Blocks of 100
+    rows (ragged last block: 1096 = 10 * 100 + 96) and of 1 row; the second build reuses the buffer."""
     system = clusters.workload("water8")
     rng = np.random.default_rng(8)
     with lib.Handle(system) as h:
@@ -109,12 +110,14 @@ def test_blocked_slices_match_resident_slices(lib):
         resident = _k(h, lib, D, C, 5, tc=True)
     with lib.Handle(system) as h:
         h.build_B()
-        os.environ["DFHF_SPLIT_BLOCK_ROWS"] = "100"
+        os.environ["DFHF_SPLIT_BLOCK_ROWS"] = rows
         try:
             blocked5 = _k(h, lib, D, C, 5, tc=True)
             blocked3 = _k(h, lib, D, C, 3, tc=True)
+            again5 = _k(h, lib, D, C, 5, tc=True)
         finally:
             del os.environ["DFHF_SPLIT_BLOCK_ROWS"]
     assert np.array_equal(blocked5, resident)
+    assert np.array_equal(again5, resident)
     scale = np.abs(K64).max()
     assert np.abs(blocked3 - K64).max() <= 2.0 ** (7 - 21) * scale
