@@ -115,15 +115,17 @@ int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_s
  * length of one packed row of B (doubles). Any pointer may be NULL. */
 int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed_row);
 
-/* Three-centre integrals (P|mu nu) per angular-momentum class, metric Cholesky (P|Q) = L L^T and
- * whitening B = L^-1 (Q|mu nu), stored packed (mu >= nu tiles) and kept in HBM.
+/* Three-centre integrals (P|mu nu) per angular-momentum class by Rys quadrature (paper, section
+ * "Molecular integrals"), metric Cholesky (P|Q) = L L^T and whitening B = L^-1 (Q|mu nu) (eq. 1, third
+ * form, M' = L^-1), stored packed (mu >= nu tiles) and kept in HBM (section "Density fitting utilities").
+ * L^-1 is formed once in FP64; the whitening applies it as a 7-slice split-precision product.
  * Returns DF_E_NOMEM if the packed tensors do not fit; DF_E_NUMERIC if (P|Q) is not positive definite.
  * screen_tau as in df_options (0 = compute every triple). keep_3c = 1 keeps the unwhitened tensor
  * for df_get_rows (needs twice the memory). */
 int df_build_B(df_handle* h, double screen_tau, int keep_3c);
 
-/* Coulomb and exchange matrices for density D (n x n, symmetric) and occupied coefficients
- * C_occ (n x nocc, row-major: C_occ[mu * nocc + i]):
+/* Coulomb and exchange matrices (paper eq. 3, first two forms, and eqs. 1-2, first forms) for density
+ * D (n x n, symmetric) and occupied coefficients C_occ (n x nocc, row-major: C_occ[mu * nocc + i]):
  *   J = sum_P gamma_P B_P with gamma_P = sum B_{P,mu nu} D_{mu nu};  K = sum_{P,i} Y Y^T.
  * J and K are n x n outputs. device_ptrs = 1: all four are device pointers (on the handle's device);
  * 0: host pointers, copied in and out inside the call. precision: DF_PREC_FP64 or DF_PREC_SPLIT
@@ -131,15 +133,17 @@ int df_build_B(df_handle* h, double screen_tau, int keep_3c);
 int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* J, double* K,
           int device_ptrs, int precision, int slices);   /* slices: 2..5 for DF_PREC_SPLIT */
 
-/* Full SCF from the core-Hamiltonian guess; builds B first if needed (screen_tau from opts).
+/* Full RHF SCF (paper, section "Standard algorithms": the Fock builder uses density fitting) from the
+ * core-Hamiltonian guess; builds B first if needed (screen_tau from opts).
  * Results in *out; returns out->status. */
 int scf_run(df_handle* h, const df_options* opts, df_result* out);
 
-/* Batched SCF: nmol independent molecules (distinct handles on one device) solved together. Every
- * iteration enqueues all unfinished molecules' work on their own streams before waiting on any, so
- * kernels of different molecules overlap on the GPU; each molecule needs one host synchronisation per
- * iteration (its energy and error). B is built first for handles that lack it. out[i] receives
- * molecule i's result; the return value is DF_OK if all converged, else the first failing status. */
+/* Batched SCF: nmol independent molecules (distinct handles on one device) solved together. Each
+ * molecule's iteration is enqueued on its own stream; one host thread polls the molecules' completion
+ * events and advances whichever has finished (convergence test, DIIS, orbital step, next iteration),
+ * starting one more molecule per pass, so kernels of different molecules overlap on the GPU. B is built
+ * first for handles that lack it. out[i] receives molecule i's result; the return value is DF_OK if all
+ * converged, else the first failing status. */
 int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out);
 
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
