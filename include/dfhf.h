@@ -73,7 +73,8 @@ typedef struct {
                                 occupied orbitals of both densities (QR of [C, C_ref], 2 nocc x 2 nocc
                                 eigenproblem) and built at 3 slices; D_ref is rebuilt in full every 8
                                 iterations. 0: every iteration builds K in full. */
-    double screen_tau;       /* drop shell triples whose bound is below tau (0 = none) */
+    double screen_tau;       /* Schwarz screening threshold: validated (>= 0, else DF_E_ARG) but not
+                                applied; every shell triple is computed (the FP64 parity bar needs 0) */
     int approx_diag;         /* 1: late iterations (max|e| < 1e-4) rotate the previous orbitals by
                                 kappa_ia = F'_ia / (eps_a - eps_i) (approximate diagonalisation, Stewart,
                                 Csaszar and Pulay 1982) instead of a full eigensolve; every 8th late
@@ -120,7 +121,7 @@ int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed
  * form, M' = L^-1), stored packed (mu >= nu tiles) and kept in HBM (section "Density fitting utilities").
  * L^-1 is formed once in FP64; the whitening applies it as a 7-slice split-precision product.
  * Returns DF_E_NOMEM if the packed tensors do not fit; DF_E_NUMERIC if (P|Q) is not positive definite.
- * screen_tau as in df_options (0 = compute every triple). keep_3c = 1 keeps the unwhitened tensor
+ * screen_tau as in df_options (must be >= 0; every triple is computed). keep_3c = 1 keeps the unwhitened tensor
  * for df_get_rows (needs twice the memory). */
 int df_build_B(df_handle* h, double screen_tau, int keep_3c);
 
