@@ -240,9 +240,10 @@ int df_set_stream(df_handle* h, void* stream);
  * [0] 1e+metric, [1] three-centre ERI, [2] Cholesky+inverse, [3] whitening, [4] gamma, [5] J,
  * [6] Y half-transform (FP64), [7] K contraction (FP64), [8] whole split exchange, [9] split Y,
  * [10] split K contraction, [11] split slicing and reduction, [12] tile width of the tensor-core Y
- * kernel and [15] K tile width chosen by the autotuner, [13] K split (occupancy heuristic), [14] time the
- * process has spent autotuning, [16] kernel launches of the last J/K build, [17] metric Cholesky factorisation and [18]
- * inversion of its factor (both within [2]). Up to `count` (<= 20) values are written. */
+ * kernel and [15] K tile width chosen by the autotuner, [13] K split (occupancy heuristic), [14] time
+ * the process has spent autotuning, [16] kernel launches of the last J/K build, [17] metric Cholesky
+ * factorisation and [18] inversion of its factor (both within [2]). Up to `count` (<= 20) values are
+ * written. */
 int df_timings(const df_handle* h, double* ms, int count);
 
 void df_free(df_handle* h);
