@@ -126,9 +126,69 @@ def _peaks():
 # keyed by (workload, kernel, slices, tile width). Anything not captured reports null.
 NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.588e9 + 8.975e9, ("water32", "K", 5, 32): 72.219e9 + 0.044e9}
 
-# FP64 DFMA peak of GB300 measured with a dependent-chain-free DFMA loop over all 152 SMs
-# (1.00 TFLOP/s; DMMA m8n8k4 gave 1.05 TFLOP/s).
-FP64_PEAK_TFLOPS = 1.00
+def core_density(h):
+    """A physical density for the timed builds: the core-Hamiltonian orbitals of the handle's molecule."""
+    S_ov, H = h.matrix("S"), h.matrix("H")
+    sv, U = np.linalg.eigh(S_ov)
+    X = U[:, sv > 1e-7] / np.sqrt(sv[sv > 1e-7])
+    _, Cp = np.linalg.eigh(X.T @ H @ X)
+    C = np.ascontiguousarray((X @ Cp)[:, :h.nocc])
+    return C, 2 * C @ C.T
+
+
+def _scf_info(res):
+    return {"energy": res["energy"], "iterations": res["iterations"], "converged": bool(res["converged"]),
+            "t_total_s": res["t_total_s"], "t_build_s": res["t_build_s"], "t_iter_s": res["t_iter_s"],
+            "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"],
+            "incremental_builds": res["incremental_builds"], "approx_steps": res["approx_steps"]}
+
+
+def fp64_peak(binding, gpu_index):
+    """The FP64 pipe's rate on this GPU, measured now (DFMA and FP64 mma.sync loops of about 1 s each) with
+    the SM clock sampled meanwhile: the denominator of the FP64 kernels' roofline fractions."""
+    with ClockSampler(gpu_index) as clk:
+        dfma, ms_a = binding.fp64_rate(0, 480000)
+        dmma, ms_b = binding.fp64_rate(1, 120000)
+    c = clk.summary()
+    out = {"dfma_tflops": dfma, "dmma_tflops": dmma, "peak_tflops": max(dfma, dmma),
+           "timed_ms": [ms_a, ms_b], "clocks": c,
+           "how": "df_fp64_rate: 4 CTAs x 256 threads per SM; DFMA 8 independent chains per thread, "
+                  "DMMA 4 independent m8n8k4 accumulations per warp; 2 flops per multiply-add"}
+    if c.get("sm_mhz"):
+        out["fp64_flops_per_sm_per_clock"] = max(dfma, dmma) * 1e12 / (152 * c["sm_mhz"] * 1e6)
+    return out
+
+
+def jk_steps(h, lib, dev, stream, D, C, precision, slices, warmup, steps, ws=1):
+    """Device-timed J/K builds from resident D and C (CUDA events on the stream the library launches on);
+    returns (ms per build, per-build phase timings, the last K as a device tensor)."""
+    import torch
+    import torch.distributed as tdist
+    n, nocc = h.n, C.shape[1]
+    dD = torch.from_numpy(D).to(dev)
+    dC = torch.from_numpy(np.ascontiguousarray(C)).to(dev)
+    dJ = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dK = torch.empty((n, n), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
+    try:
+        for _ in range(warmup):
+            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
+        torch.cuda.synchronize()
+        if ws > 1:
+            tdist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per = []
+        ev0.record(stream)
+        for _ in range(steps):
+            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
+            per.append(dict(h.timings()))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        lib.df_set_stream(h.h, None)
+    total = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    return total / steps, per, dK
 
 
 def gpu_arm(args):
@@ -148,58 +208,29 @@ def gpu_arm(args):
     lib = binding.load()
     system = clusters.workload(args.workload)
     guess_net = None
+    learned = None
     if args.ttc and args.learned > 0:
         guess_net, learned = learned_guess_net(binding, clusters, args.learned)
     split = args.precision == "split"
     prec = binding.DF_PREC_SPLIT if split else binding.DF_PREC_FP64
     S = args.slices
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
 
     t0 = time.perf_counter()
     h = binding.Handle(system)
-    h.build_B()
+    h.build_B(whitening=None if split else binding.DF_WHITEN_FP64)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     build_ms = h.timings()
-
-    # a physical density for the timed builds: the core-Hamiltonian orbitals
     n, nocc = h.n, h.nocc
-    S_ov, H = h.matrix("S"), h.matrix("H")
-    sv, U = np.linalg.eigh(S_ov)
-    X = U[:, sv > 1e-7] / np.sqrt(sv[sv > 1e-7])
-    _, Cp = np.linalg.eigh(X.T @ H @ X)
-    C = np.ascontiguousarray((X @ Cp)[:, :nocc])
-    D = 2 * C @ C.T
-    dev = torch.device("cuda", local)
-    dD = torch.from_numpy(D).to(dev)
-    dC = torch.from_numpy(C).to(dev)
-    dJ = torch.empty((n, n), dtype=torch.float64, device=dev)
-    dK = torch.empty((n, n), dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    torch.cuda.synchronize()
-    lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
-
-    def run_steps(precision, slices, warmup, steps):
-        for _ in range(warmup):
-            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
-        torch.cuda.synchronize()
-        if ws > 1:
-            tdist.barrier()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        per = []
-        ev0.record(stream)
-        for _ in range(steps):
-            h.jk_device(dD.data_ptr(), dC.data_ptr(), nocc, dJ.data_ptr(), dK.data_ptr(), precision, slices)
-            per.append(dict(h.timings()))
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        total = max_over_ranks(ev0.elapsed_time(ev1), dev)
-        return total / steps, per
+    C, D = core_density(h)
 
     with ClockSampler(local) as clocks:
-        ms_per_step, per = run_steps(prec, S, args.warmup, args.steps)
+        ms_per_step, per, dK_main = jk_steps(h, lib, dev, stream, D, C, prec, S, args.warmup, args.steps, ws)
+    K_main = dK_main.clone()
 
     # end to end through the C ABI with host buffers (copies in and out inside the timed region)
-    lib.df_set_stream(h.h, None)
     for _ in range(2):
         Jh, Kh = h.jk(D, C, prec, S)
     torch.cuda.synchronize()
@@ -207,69 +238,95 @@ def gpu_arm(args):
     for _ in range(args.steps):
         Jh, Kh = h.jk(D, C, prec, S)
     e2e_s = max_over_ranks((time.perf_counter() - t1) / args.steps, dev)
-    lib.df_set_stream(h.h, ctypes_ptr(stream.cuda_stream))
 
-    # comparisons: the other precisions on the same density
+    # comparisons on the same density: the early split form (3 slices) and the FP64 form, and the accuracy
+    # of the split exchange against the FP64 exchange on the same B
     compare = {}
+    k_accuracy = None
     if split:
-        compare["split_s3_s_per_iter"] = run_steps(binding.DF_PREC_SPLIT, 3, 1, 3)[0] / 1000.0
+        ms3, _, dK3 = jk_steps(h, lib, dev, stream, D, C, binding.DF_PREC_SPLIT, 3, 1, 3)
+        compare["split_s3_s_per_iter"] = ms3 / 1000.0
+        K3 = dK3.clone()
         if not args.no_fp64_compare:
-            compare["fp64_s_per_iter"] = run_steps(binding.DF_PREC_FP64, 0, 1, 2)[0] / 1000.0
-    lib.df_set_stream(h.h, None)
+            ms64, _, dK64 = jk_steps(h, lib, dev, stream, D, C, binding.DF_PREC_FP64, 0, 1, 2)
+            compare["fp64_s_per_iter"] = ms64 / 1000.0
+            kmax = float(dK64.abs().max())
+            k_accuracy = {"density": "core-Hamiltonian orbitals", "max_abs_K": kmax,
+                          f"S{S}_max_rel_dK_vs_fp64": float((K_main - dK64).abs().max()) / kmax,
+                          "S3_max_rel_dK_vs_fp64": float((K3 - dK64).abs().max()) / kmax}
 
     # time to a converged SCF from the core-Hamiltonian guess (B already built: its build time is added),
     # and from the learned guess (network trained beforehand on smaller clusters; training not timed)
-    ttc = {}
-    scf_info = {}
-    if guess_net is None:
-        learned = None
+    ttc, scf_info, hist = {}, {}, {}
     if args.ttc:
         # split precision: S = 3 early, then a 5-slice reference K every 8 iterations with 3-slice
         # density-change builds in between (incremental Fock); "_full" keeps full 5-slice builds
         inc = 1 if split else 0
-        runs = [("split" if split else "fp64", prec, None, inc)]   # late: incremental Fock, approximate diagonalisation
+        runs = [("split" if split else "fp64", prec, None, inc)]
         if guess_net is not None:
             t0 = time.perf_counter()
             D0 = h.mlp_guess(guess_net, bf16=True)
             t_guess = time.perf_counter() - t0
-            guess_net.close()
             learned["t_guess_s"] = t_guess
             runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess), inc))
             if split:
                 runs.append(("split_learned_full", prec, (D0, t_guess), 0))
-        if split and args.compare_ttc:
-            runs.append(("fp64", binding.DF_PREC_FP64, None, 0))
-        hist = {}
-        for label, p, g, inc in runs:
-            res = h.scf(precision=p, slices=3, incremental=inc, approx_diag=inc, guess=None if g is None else g[0])
+        for label, p, g, inc_ in runs:
+            res = h.scf(precision=p, slices=3, incremental=inc_, approx_diag=inc_, guess=None if g is None else g[0])
             hist[label] = h.history()[:, 1]
             ttc[label] = t_build + res["t_total_s"] + (0.0 if g is None else g[1])
-            scf_info[label] = {"energy": res["energy"], "iterations": res["iterations"],
-                               "converged": bool(res["converged"]), "t_iter_s": res["t_iter_s"],
-                               "t_jk_s": res["t_jk_s"], "ramp_iteration": res["ramp_iteration"],
-                               "incremental_builds": res["incremental_builds"], "approx_steps": res["approx_steps"]}
-
-    # split vs FP64 from the same core-Hamiltonian guess: energy difference iteration by iteration
-    de_iter = None
-    if args.ttc and split and args.compare_ttc:
-        a, b = hist["split"], hist["fp64"]
-        m = min(len(a), len(b))
-        de_iter = {"per_iteration": [float(f"{x:.3e}") for x in (a[:m] - b[:m])],
-                   "at_convergence": float(scf_info["split"]["energy"] - scf_info["fp64"]["energy"])}
+            scf_info[label] = _scf_info(res)
 
     peaks, peak_src = _peaks()
     keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
             "split_other_ms"]
     avg = {k: float(np.mean([d[k] for d in per])) for k in keys}
     naux = h.naux
+    b_bytes = naux * h.packed_row * 8.0
+    packed_gb = h.naux * h.packed_row * 8 / 1e9
+    tuned = per[-1]
+    h.close()
+
+    # the plain FP64 path end to end: B whitened in FP64, FP64 exchange, full eigensolves, from the
+    # core-Hamiltonian guess; then the split SCF on that same B (energy difference due to the exchange's
+    # precision alone)
+    de = None
+    if split and args.ttc and not args.no_fp64_ttc:
+        with binding.Handle(system) as h64:
+            res64 = h64.scf()
+            hist["fp64"] = h64.history()[:, 1]
+            ttc["fp64"] = res64["t_total_s"]
+            scf_info["fp64"] = dict(_scf_info(res64), whitening="fp64", exchange="fp64")
+            res_s = h64.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1)
+            h_s = h64.history()[:, 1]
+        a, b = h_s, hist["fp64"]
+        m = min(len(a), len(b))
+        de = {"same_B": {"B": "FP64 whitening", "at_convergence": float(res_s["energy"] - res64["energy"]),
+                         "split_iterations": res_s["iterations"], "fp64_iterations": res64["iterations"],
+                         "per_iteration": [float(f"{x:.3e}") for x in (a[:m] - b[:m])]},
+              "split_vs_plain_fp64": {"at_convergence": float(scf_info["split"]["energy"] - res64["energy"]),
+                                      "note": "split SCF on the tensor-core-whitened B against the plain FP64 "
+                                              "path (FP64 whitening and exchange)"}}
+        if "split_learned" in scf_info:
+            de["split_learned_vs_plain_fp64"] = {"at_convergence": float(scf_info["split_learned"]["energy"]
+                                                                         - res64["energy"])}
+
+    # the 40-water configuration (n=2000, naux=5480, nocc=200): split J/K and time to converge
+    c2 = None
+    if split and args.ttc and args.c2:
+        c2 = c2_measure(args, binding, clusters, lib, dev, stream, guess_net)
+    if guess_net is not None:
+        guess_net.close()
+
+    fp64pk = fp64_peak(binding, local)
+    fp64_peak_tf = fp64pk["peak_tflops"]
     alg_k_flops = 2.0 * naux * n * n * nocc + 1.0 * naux * n * n * nocc   # Y = B C and K = sum Y Y^T
     if not split:
         flops = 2.0 * naux * n * n * nocc
         achieved = flops / (avg["ytransform_ms"] * 1e-3) / 1e12
         roofline = {"kernel": "y_transform_kernel (FP64 DFMA)", "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "measured FP64 DFMA loop over 152 SMs (not in MEASURED_PEAKS.json)",
-                    "traffic": None}
+                    "peak": fp64_peak_tf, "unit": "TFLOP/s", "frac": achieved / fp64_peak_tf,
+                    "peak_source": "FP64 rate measured in this run (fp64_peak)", "traffic": None}
     else:
         npad = (n + 63) // 64 * 64
         ldy = (nocc + 31) // 32 * 32
@@ -285,8 +342,7 @@ def gpu_arm(args):
         tc = os.environ.get("DFHF_SPLIT_TC", "1") != "0" and S in (3, 5)
         kname = ("ozaki_tc_kernel<Y>" if dom_y else "ozaki_tc_kernel<K>") + " (tcgen05 BF16, TMEM, TMA)" if tc else \
             ("y_split_kernel" if dom_y else "k_split_kernel") + " (BF16 mma.sync)"
-        tuned_tiles = per[-1]
-        tile = int(tuned_tiles.get("tc_y_tile_n" if dom_y else "tc_k_tile_n", 0))
+        tile = int(tuned.get("tc_y_tile_n" if dom_y else "tc_k_tile_n", 0))
         traffic = NCU_TRAFFIC.get((args.workload, "Y" if dom_y else "K", S, tile)) if tc else None
         roofline = {"kernel": kname + ", Ozaki slices",
                     "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
@@ -297,33 +353,35 @@ def gpu_arm(args):
                     "algorithmic_bytes": (S * naux * npad * npad * 2 + naux * npad * ldy * 8) if dom_y else
                                          (S * naux * npad * ldy * 2),
                     "y_split_tflops": y_tf, "k_split_tflops": k_tf,
+                    "k_split_frac": k_tf / pk if pk else None,
                     "fp64_equivalent_tflops": alg_k_flops / ((avg["split_y_ms"] + avg["split_k_ms"] + avg["split_other_ms"]) * 1e-3) / 1e12}
     kernel_ms = {k: round(v, 3) for k, v in avg.items()}
-    # the other rows' rooflines: DF-J reads packed B twice (gamma, coulomb) against HBM; the integral
-    # kernels write packed (P|mu nu) once (FP64 ALU bound); whitening counts naux^2 * npair FP64-equivalent
-    # flops (run as 7-slice BF16 products on the tensor cores unless the float-float form is selected)
-    b_bytes = naux * h.packed_row * 8.0
+    # the other rows' rooflines: DF-J reads packed B twice (gamma, coulomb) against HBM and does one FMA per
+    # element read against the FP64 pipe; the integral kernels write packed (P|mu nu) once (FP64 ALU bound);
+    # whitening counts naux^2 * npair FP64-equivalent flops
     npair = n * (n + 1) // 2
     hbm = peaks.get("hbm_gbs")
-    j_gbs = 2.0 * b_bytes / ((avg["gamma_ms"] + avg["coulomb_ms"]) * 1e-3) / 1e9
+    j_s = (avg["gamma_ms"] + avg["coulomb_ms"]) * 1e-3
+    j_gbs = 2.0 * b_bytes / j_s / 1e9
+    j_tf = 2.0 * 2.0 * naux * h.packed_row / j_s / 1e12
     eri_s = build_ms["eri3c_ms"] * 1e-3
     n_triples = int(len(system.aux)) * (len(system.basis) * (len(system.basis) + 1) // 2)
     wh_s = build_ms["whiten_ms"] * 1e-3
     other_rooflines = {
-        "df_j": {"kernels": "gamma_kernel + coulomb_kernel (FP64)", "bound": "hbm",
-                 "algorithmic_bytes": 2.0 * b_bytes, "achieved": j_gbs, "peak": hbm, "unit": "GB/s",
-                 "frac": j_gbs / hbm if hbm else None, "peak_source": f"{peak_src} hbm_gbs"},
+        "df_j": {"kernels": "gamma_kernel + coulomb_kernel (FP64)", "bound": "alu",
+                 "algorithmic_bytes": 2.0 * b_bytes, "achieved_gbs": j_gbs, "hbm_peak": hbm,
+                 "hbm_frac": j_gbs / hbm if hbm else None, "peak_source": f"{peak_src} hbm_gbs",
+                 "fp64_tflops": j_tf, "fp64_frac": j_tf / fp64_peak_tf},
         "eri3c": {"kernels": "eri3c_kernel (FP64 Rys)", "bound": "alu",
                   "shell_triples": n_triples, "gtriples_per_s": n_triples / eri_s / 1e9,
                   "write_bytes": naux * npair * 8.0, "write_gbs": naux * npair * 8.0 / eri_s / 1e9,
                   "write_frac_of_hbm": naux * npair * 8.0 / eri_s / 1e9 / hbm if hbm else None},
-        "whitening": {"kernels": "ozaki_tc_kernel<W> (tcgen05 BF16, 7 slices)"
-                      if os.environ.get("DFHF_WHITEN", "tc") != "ff" else "float-float mma.sync",
+        "whitening": {"kernels": ("ozaki_tc_kernel<W> (tcgen05 BF16, 7 slices)" if split else
+                                  "dgemm_kernel (FP64 DFMA, in place by 64-row blocks)"),
                       "fp64_equivalent_flops": float(naux) * naux * npair,
                       "fp64_equivalent_tflops": float(naux) * naux * npair / wh_s / 1e12,
-                      "vs_fp64_peak": float(naux) * naux * npair / wh_s / 1e12 / FP64_PEAK_TFLOPS},
+                      "vs_fp64_peak": float(naux) * naux * npair / wh_s / 1e12 / fp64_peak_tf},
     }
-    tuned = per[-1]
     autotune = {"y_tile_n": int(tuned.get("tc_y_tile_n", 0)), "k_tile_n": int(tuned.get("tc_k_tile_n", 0)),
                 "k_split": int(tuned.get("tc_k_split", 0)),
                 "tuning_ms_this_process": round(float(tuned.get("autotune_ms", 0.0)), 1)} if split else None
@@ -339,7 +397,7 @@ def gpu_arm(args):
         "dtype": f"bf16 Ozaki x{S} slices, exact f32 chunk sums, f32x2 accumulate, f64 J" if split else "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: seeded water cluster, n={n}, naux={naux}, nocc={nocc}, "
-                               f"packed B {h.naux * h.packed_row * 8 / 1e9:.1f} GB",
+                               f"packed B {packed_gb:.1f} GB",
                    "precision": args.precision + (f" (S={S})" if split else ""),
                    "l2": "inputs larger than L2 (B resident, no flush)",
                    "parallelism": f"replicas x{ws}"},
@@ -348,20 +406,22 @@ def gpu_arm(args):
         "gpu_launches": int(sum(d.get("jk_launches", launches_per_step(prec)) for d in per)),
         "roofline": roofline,
         "other_rooflines": other_rooflines,
+        "fp64_peak": fp64pk,
         "kernel_ms": kernel_ms,
         "autotune": autotune,
         "compare": compare,
+        "k_accuracy": k_accuracy,
         "build_B": {"wall_s": t_build, "eri3c_ms": build_ms["eri3c_ms"], "cholesky_ms": build_ms["cholesky_ms"],
                     "potrf_ms": build_ms.get("potrf_ms"), "trtri_ms": build_ms.get("trtri_ms"),
                     "whiten_ms": build_ms["whiten_ms"], "init_ms": build_ms["init_ms"],
                     "eri_triples": n_triples},
-        "time_to_converge_s": ttc or None, "scf": scf_info or None, "dE_split_vs_fp64": de_iter,
+        "time_to_converge_s": ttc or None, "scf": scf_info or None, "dE_split_vs_fp64": de,
+        "c2_water40": c2,
         "batched": None,
         "learned_guess": learned,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
-    h.close()
     # many small clusters, after the large cluster's tensors have left the device
     if args.batch > 0:
         line["batched"] = batched_measure(binding, clusters, args.batch, torch, rank, dev, args.batch_max_waters)
@@ -369,6 +429,43 @@ def gpu_arm(args):
         print(json.dumps(line))
     if ws > 1:
         tdist.destroy_process_group()
+
+
+def c2_measure(args, binding, clusters, lib, dev, stream, guess_net):
+    """The 40-water cluster (n=2000, naux=5480, nocc=200): B build, split J/K per iteration (5 and 3 slices)
+    and one FP64 J/K build on the same density, then split SCFs to convergence from the core-Hamiltonian and
+    the learned guess (incremental Fock and approximate diagonalisation late)."""
+    import torch
+    system = clusters.workload("water40")
+    out = {"workload": f"water40: seeded water cluster, n={system.nbf}, naux={system.naux}, nocc={system.nocc}"}
+    t0 = time.perf_counter()
+    with binding.Handle(system) as h:
+        h.build_B()
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        bms = h.timings()
+        out["build_B"] = {"wall_s": t_build, "eri3c_ms": bms["eri3c_ms"], "cholesky_ms": bms["cholesky_ms"],
+                          "whiten_ms": bms["whiten_ms"]}
+        out["packed_B_gb"] = h.naux * h.packed_row * 8 / 1e9
+        C, D = core_density(h)
+        ms5, per5, _ = jk_steps(h, lib, dev, stream, D, C, binding.DF_PREC_SPLIT, 5, 1, 3)
+        ms3, _, _ = jk_steps(h, lib, dev, stream, D, C, binding.DF_PREC_SPLIT, 3, 1, 2)
+        ms64, _, _ = jk_steps(h, lib, dev, stream, D, C, binding.DF_PREC_FP64, 0, 0, 1)
+        out["jk_s_per_iter"] = {"split_s5": ms5 / 1000, "split_s3": ms3 / 1000, "fp64": ms64 / 1000}
+        out["split_s5_kernel_ms"] = {k: round(float(np.mean([d[k] for d in per5])), 3)
+                                     for k in ("gamma_ms", "coulomb_ms", "split_y_ms", "split_k_ms", "split_other_ms")}
+        res = h.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1)
+        out["ttc_split_s"] = t_build + res["t_total_s"]
+        out["scf_split"] = _scf_info(res)
+        if guess_net is not None:
+            t1 = time.perf_counter()
+            D0 = h.mlp_guess(guess_net, bf16=True)
+            t_guess = time.perf_counter() - t1
+            res_l = h.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1, guess=D0)
+            out["ttc_split_learned_s"] = t_build + res_l["t_total_s"] + t_guess
+            out["scf_split_learned"] = _scf_info(res_l)
+            out["dE_learned_vs_core"] = res_l["energy"] - res["energy"]
+    return out
 
 
 def train_guess(binding, clusters, members, epochs=200, precision=None):
@@ -571,6 +668,10 @@ def cpu_baseline(system, budget_s=15.0):
 
 
 def reference_arm(args):
+    """The oracle (numpy DF J/K, eqs. 1-3) on the host cores. One step times the oracle's J and K on a
+    bounded sample of 4 auxiliary rows of the workload; `value` scales the per-row cost to all naux rows
+    (the cost of eqs. 1-3 is linear in naux), while `ms_per_step` is the measured time of the sampled
+    step, so steps x ms_per_step is the timed region."""
     ws, rank = _dist()
     if rank != 0:
         return
@@ -580,17 +681,20 @@ def reference_arm(args):
     rows = 4
     for _ in range(args.warmup):
         _oracle_jk_sample(system, rows, rng)
-    times = [_oracle_jk_sample(system, rows, rng) / rows * system.naux for _ in range(args.steps)]
-    v = float(np.mean(times))
+    t = [_oracle_jk_sample(system, rows, rng) for _ in range(args.steps)]
+    v = float(np.mean(t)) / rows * system.naux
     cores = os.cpu_count()
+    sample = (f"oracle df_J + df_K on {rows} of {system.naux} auxiliary rows per step "
+              f"({float(np.mean(t)):.2f} s measured per step), scaled by naux/{rows}")
     line = {"metric": METRIC, "value": v, "unit": "s/iter (DF J+K build)", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v * 1000, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": float(np.mean(t)) * 1000, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "extrapolated": {"measured_rows_per_step": rows, "naux": system.naux,
+                             "value_is": "measured time per row x naux"},
             "config": {"workload": f"{args.workload}: seeded water cluster, n={system.nbf}, naux={system.naux}, "
                                    f"nocc={system.nocc}", "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": "s/iter (DF J+K build)", "cores": cores, "kind": "oracle",
-                             "sample": f"oracle df_J + df_K on {rows} of {system.naux} auxiliary rows per step, "
-                                       f"scaled by naux/{rows}"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "s/iter (DF J+K build)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -605,7 +709,9 @@ def main():
     ap.add_argument("--precision", default="split", choices=["fp64", "split"])
     ap.add_argument("--slices", type=int, default=5, help="slices of the timed split builds (the late-SCF precision)")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--compare-ttc", action="store_true", help="also time a full FP64 SCF (minutes)")
+    ap.add_argument("--no-fp64-ttc", action="store_true",
+                    help="skip the plain FP64 SCF to convergence (FP64 whitening and exchange; minutes)")
+    ap.add_argument("--no-c2", dest="c2", action="store_false", help="skip the 40-water measurement")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false")
     ap.add_argument("--batch", type=int, default=16, help="molecules in the batched-SCF measurement (0: skip)")
     ap.add_argument("--batch-max-waters", type=int, default=8, help="cluster sizes 1..W in the batched measurement")

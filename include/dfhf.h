@@ -125,6 +125,15 @@ int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed
  * for df_get_rows (needs twice the memory). */
 int df_build_B(df_handle* h, double screen_tau, int keep_3c);
 
+/* How the whitening B = L^-1 (Q|mu nu) is applied (the metric factor and its inverse are FP64 either way). */
+#define DF_WHITEN_SPLIT 0    /* 7-slice split-precision product on the tensor cores (df_build_B's choice) */
+#define DF_WHITEN_FP64 1     /* FP64 product on the FP64 pipe: slower (about 20 s at n = 1600, naux = 4384)
+                                but FP64 end to end; scf_run builds B this way for DF_PREC_FP64 */
+
+/* df_build_B with the whitening chosen (DF_WHITEN_*); a different value gives DF_E_ARG. Rebuilding B
+ * drops the split-precision slices cut from the previous B. */
+int df_build_B_ex(df_handle* h, double screen_tau, int keep_3c, int whitening);
+
 /* Coulomb and exchange matrices (paper eq. 3, first two forms, and eqs. 1-2, first forms) for density
  * D (n x n, symmetric) and occupied coefficients C_occ (n x nocc, row-major: C_occ[mu * nocc + i]):
  *   J = sum_P gamma_P B_P with gamma_P = sum B_{P,mu nu} D_{mu nu};  K = sum_{P,i} Y Y^T.
@@ -135,7 +144,8 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
           int device_ptrs, int precision, int slices);   /* slices: 2..5 for DF_PREC_SPLIT */
 
 /* Full RHF SCF (paper, section "Standard algorithms": the Fock builder uses density fitting) from the
- * core-Hamiltonian guess; builds B first if needed (screen_tau from opts).
+ * core-Hamiltonian guess; builds B first if needed (screen_tau from opts; DF_WHITEN_FP64 for
+ * DF_PREC_FP64, DF_WHITEN_SPLIT for DF_PREC_SPLIT).
  * Results in *out; returns out->status. */
 int scf_run(df_handle* h, const df_options* opts, df_result* out);
 
@@ -220,13 +230,22 @@ int df_rint_pow2(const double* v, const int* k, long long count, long long* out)
  * application that owns all device memory through its own allocator, or a latency-critical loop that
  * cannot afford an allocation's synchronisation or failure). Same kernels and result as the J of
  * df_jk; the scratch (packed density, gamma, packed J) lives in a 48 MiB array inside the library,
- * which every GPU that loads the library holds until exit. Requires df_build_B. Systems needing more
- * than 6,291,456 doubles of scratch (2 packed rows of B + naux; about n <= 2400) are rejected with
- * DF_E_ARG and a message in df_last_error. Work is enqueued on the handle's stream and the call returns
- * without waiting. The first call on a device looks up the array's device address (once per device),
- * so make that first call before any stream capture. All calls share the array: calls that overlap on
- * the GPU race; calls ordered on one stream are safe. */
+ * which every GPU that loads the library holds until exit. df_init resolves the array's device address
+ * for the handle's device (under lazy module loading this is what commits the array's memory) and
+ * loads the Coulomb kernels, so this call itself allocates nothing; if df_init could not resolve the
+ * address, this call returns DF_E_STATE with the reason in df_last_error. Requires df_build_B. Systems
+ * needing more than 6,291,456 doubles of scratch (2 packed rows of B + naux; about n <= 2400) are
+ * rejected with DF_E_ARG and a message in df_last_error. Work is enqueued on the handle's stream and the
+ * call returns without waiting. All calls share the array: calls that overlap on the GPU race; calls
+ * ordered on one stream are safe. Every failure sets df_last_error. */
 int df_coulomb_noalloc(df_handle* h, const double* D, double* J);
+
+/* Measured FP64 rate of the current device, the denominator of the FP64 kernels' roofline (the paper has no
+ * counterpart): kind 0 times a DFMA loop (8 independent chains per thread), kind 1 an mma.sync m8n8k4 FP64
+ * loop, each `iters` iterations over 4 CTAs of 256 threads per SM after a short warm-up launch. *tflops
+ * receives 2 x multiply-adds / time, *ms (may be NULL) the timed launch's duration. Allocates a small sink
+ * array. Returns DF_E_ARG for another kind, iters < 1 or a null tflops. */
+int df_fp64_rate(int kind, long long iters, double* tflops, double* ms);
 
 /* Host-side set-up without a GPU: builds and validates the Rys root/weight table (Gauss rules of the
  * Boys-function measure) and caches it as rys_table.bin beside the library (or at $DFHF_TABLE_CACHE).

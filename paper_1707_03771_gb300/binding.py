@@ -14,12 +14,14 @@ from . import build as _build
 
 DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, DF_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
+DF_WHITEN_SPLIT, DF_WHITEN_FP64 = 0, 1
 
-EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
+EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
             "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
-            "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2"]
+            "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
+            "df_fp64_rate"]
 DF_MLP_NFEAT = 57
 
 
@@ -72,6 +74,7 @@ def load(path: str | None = None):
     L.df_init.argtypes = [P(Atom), c_int, P(Shell), c_int, P(Shell), c_int, c_int, P(c_void_p)]
     L.df_sizes.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int), P(ctypes.c_longlong)]
     L.df_build_B.argtypes = [c_void_p, c_double, c_int]
+    L.df_build_B_ex.argtypes = [c_void_p, c_double, c_int, c_int]
     L.df_jk.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_int]
     L.scf_run.argtypes = [c_void_p, P(Options), P(Result)]
     L.df_get_rows.argtypes = [c_void_p, c_int, c_int, c_int, dp]
@@ -79,6 +82,7 @@ def load(path: str | None = None):
     L.df_rys.argtypes = [dp, c_int, c_int, dp, dp]
     L.df_rint_pow2.argtypes = [dp, P(c_int), ctypes.c_longlong, P(ctypes.c_longlong)]
     L.df_prepare.argtypes = []
+    L.df_fp64_rate.argtypes = [c_int, ctypes.c_longlong, dp, dp]
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
@@ -161,8 +165,12 @@ class Handle:
         if rc != DF_OK:
             raise DFError(rc, f"{what}: {load().df_last_error(self.h).decode()}")
 
-    def build_B(self, screen_tau: float = 0.0, keep_3c: bool = False):
-        self._check(load().df_build_B(self.h, screen_tau, int(keep_3c)), "df_build_B")
+    def build_B(self, screen_tau: float = 0.0, keep_3c: bool = False, whitening: int | None = None):
+        """df_build_B, or df_build_B_ex when `whitening` (DF_WHITEN_*) is given."""
+        if whitening is None:
+            self._check(load().df_build_B(self.h, screen_tau, int(keep_3c)), "df_build_B")
+        else:
+            self._check(load().df_build_B_ex(self.h, screen_tau, int(keep_3c), int(whitening)), "df_build_B_ex")
 
     def jk(self, D, C_occ, precision=DF_PREC_FP64, slices=3):
         """J, K for host arrays D (n x n) and C_occ (n x nocc); returns numpy arrays."""
@@ -424,3 +432,13 @@ def rys(T, nroots):
     if rc != DF_OK:
         raise DFError(rc, "df_rys")
     return x, w
+
+
+def fp64_rate(kind: int = 0, iters: int = 100000):
+    """Measured FP64 rate (TFLOP/s) of the current device: kind 0 a DFMA loop, 1 an FP64 mma.sync loop.
+    Returns (tflops, milliseconds of the timed launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    rc = load().df_fp64_rate(int(kind), int(iters), ctypes.byref(t), ctypes.byref(ms))
+    if rc != DF_OK:
+        raise DFError(rc, "df_fp64_rate")
+    return t.value, ms.value

@@ -20,6 +20,8 @@ void whiten_ozaki(cudaStream_t s, int naux, long long ncol, long long ld, const 
                   double* B);
 void whiten_float_float(cudaStream_t s, int m, long long ncol, const double* Linv, double* Lff, double* A, double* B,
                         long long ld, bool restore_a);
+void coulomb_kernels_load();
+void whiten_fp64_inplace(cudaStream_t s, int m, long long ncol, const double* L, double* A, long long ld);
 
 namespace {
 
@@ -189,7 +191,7 @@ void tri_inv_lower(cudaStream_t s, double* L, int m, long long ld, double* T) {
     tri_inv_lower(s, L22, m2, ld, T);
 }
 
-void build_B(df_handle* h, double tau, bool keep) {
+void build_B(df_handle* h, double tau, bool keep, int whitening) {
     cudaStream_t s = h->stream;
     const size_t rows = (size_t)h->naux * h->pk.row;
     cudaEvent_t ev[4];
@@ -259,7 +261,19 @@ void build_B(df_handle* h, double tau, bool keep) {
     DF_CHECK_LAUNCH();
     DF_CUDA(cudaEventRecord(ev[2], s));
     const char* wenv = std::getenv("DFHF_WHITEN");
-    if (wenv && std::string(wenv) == "ff") {
+    if (whitening == DF_WHITEN_FP64) {
+        // FP64 product on the FP64 pipe, in place by 64-row blocks of L^-1 (a copy first if A is kept)
+        if (keep) {
+            h->B.alloc(rows);
+            DF_CUDA(cudaMemcpyAsync(h->B.p, h->A3c.p, sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
+        } else {
+            h->B.p = h->A3c.p;
+            h->B.n = h->A3c.n;
+            h->A3c.p = nullptr;
+            h->A3c.n = 0;
+        }
+        whiten_fp64_inplace(s, na, h->pk.row, h->Linv.p, h->B.p, h->pk.row);
+    } else if (wenv && std::string(wenv) == "ff") {
         // float-float whitening on the FP32 pipes (selectable for comparison)
         h->B.alloc(rows);
         DevBuf<double> lff;
@@ -286,6 +300,7 @@ void build_B(df_handle* h, double tau, bool keep) {
     for (auto& e : ev) cudaEventDestroy(e);
     if (!keep) h->A3c.release();
     h->built = true;
+    h->whitening = whitening;
 }
 
 void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
@@ -358,6 +373,11 @@ int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_s
         h->stream = h->own_stream;
         DF_SOLVER(cusolverDnCreate(&h->solver));
         DF_SOLVER(cusolverDnSetStream(h->solver, h->stream));
+        // df_coulomb_noalloc allocates nothing: its static scratch (address resolved here, which commits the
+        // array's memory) and its kernels are made resident on the device now; without the scratch the
+        // handle still works and that entry point reports why
+        if (noalloc_scratch_address(&h->noalloc_scratch, &h->noalloc_error) != DF_OK) h->noalloc_scratch = nullptr;
+        coulomb_kernels_load();
         h->atoms.assign(atoms, atoms + natom);
         h->basis.assign(basis, basis + nbasis_sh);
         h->aux.assign(aux, aux + naux_sh);
@@ -442,10 +462,15 @@ int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed
 }
 
 int df_build_B(df_handle* h, double screen_tau, int keep_3c) {
-    if (!h || screen_tau < 0) return DF_E_ARG;
+    return df_build_B_ex(h, screen_tau, keep_3c, DF_WHITEN_SPLIT);
+}
+
+int df_build_B_ex(df_handle* h, double screen_tau, int keep_3c, int whitening) {
+    if (!h || screen_tau < 0 || (whitening != DF_WHITEN_SPLIT && whitening != DF_WHITEN_FP64)) return DF_E_ARG;
     try {
         DF_CUDA(cudaSetDevice(h->device));
-        build_B(h, screen_tau, keep_3c != 0);
+        free_split(h);   // B slices cut from an earlier B are stale
+        build_B(h, screen_tau, keep_3c != 0, whitening);
     } catch (const Error& e) {
         h->B.release();
         h->A3c.release();

@@ -149,6 +149,7 @@ struct df_handle {
     // three-index tensors, packed rows of length pk.row
     dfhf::DevBuf<double> A3c, B;
     bool built = false;
+    int whitening = DF_WHITEN_SPLIT;   // how B was whitened (DF_WHITEN_*)
 
     // J/K work
     dfhf::DevBuf<double> Dw, gamma, Jp, Y, Kpart, Cpad, dD, dC, dJ, dK;
@@ -167,6 +168,9 @@ struct df_handle {
     bool sync_timing = true;       // per-kernel event timings (the batch driver turns them off)
     int* tc_err_host = nullptr;    // set by the SCF driver: the tensor-core kernels' timeout flag is copied
                                    // here (pinned) instead of being read back with a synchronisation
+    double* noalloc_scratch = nullptr;   // device address of the library's static Coulomb scratch array on
+                                         // this handle's device, resolved by df_init (null if that failed)
+    std::string noalloc_error;           // why it could not be resolved
 };
 
 namespace dfhf {
@@ -195,10 +199,12 @@ void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* 
 
 // split precision (split_k.cu)
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK);
-void gemm_ff(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
-             const double* B, int ldb, double beta, double* C, int ldc);
 void split_clear_error(df_handle* h);
 void free_split(df_handle* h);
+
+// static scratch of df_coulomb_noalloc (coulomb_noalloc.cu): device address of the array on the current
+// device; loads the library's module holding it if the runtime has not loaded it yet
+int noalloc_scratch_address(double** out, std::string* why);
 
 // SCF (scf.cu)
 int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess = nullptr);

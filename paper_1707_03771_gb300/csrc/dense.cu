@@ -6,6 +6,8 @@
 //   - dgemm: general row-major C = alpha op(A) op(B) + beta C (SCF algebra).
 //   - dtrmm_lower: C = L A for lower-triangular L (metric whitening B = L^-1 (Q|mu nu), paper eq. 1,
 //     third form); block rows skip the zero upper triangle.
+//   - whiten_fp64_inplace: A <- L A for lower-triangular L, in place, one 64-row block of L per launch
+//     from the last block up (the FP64 whitening).
 //   - y_transform: Y_{P,mu i} = sum_nu B_{P,mu nu} C_{nu i} reading the packed symmetric B
 //     (paper eq. 1, first form); each stored off-diagonal tile serves both (I,J) and (J,I).
 //   - k_syrk: K_{mu nu} = sum_{P,i} Y_{P,mu i} Y_{P,nu i} over lower tile pairs with split-K partial
@@ -191,6 +193,25 @@ void dtrmm_lower(cudaStream_t s, int m, long long ncol, const double* L, const d
         dim3 grid((unsigned)((nc + BN - 1) / BN), (m + BM - 1) / BM);
         dgemm_kernel<<<grid, NTHR, 0, s>>>(false, false, m, (int)nc, m, 1.0, L, m, A + c0, ld, 0.0, C + c0, ld, true);
         DF_CHECK_LAUNCH();
+    }
+}
+
+// A <- L A in place for lower-triangular L (m x m, row-major) and A (m x ncol, row stride ld). Row block I
+// of the result needs rows 0 .. end of block I of A; launching the blocks from the last one up leaves those
+// rows unmodified until their own launch. Within a launch a CTA reads only its own column tile and writes it
+// after its last read, so no CTA sees another's output.
+void whiten_fp64_inplace(cudaStream_t s, int m, long long ncol, const double* L, double* A, long long ld) {
+    const long long chunk = 65535LL * BN;   // grid.x limit
+    for (int r0 = ((m - 1) / BM) * BM; r0 >= 0; r0 -= BM) {
+        const int rows = m - r0 < BM ? m - r0 : BM;
+        const int kk = r0 + rows;   // L is zero beyond the diagonal block
+        for (long long c0 = 0; c0 < ncol; c0 += chunk) {
+            const long long nc = (ncol - c0 < chunk) ? ncol - c0 : chunk;
+            dim3 grid((unsigned)((nc + BN - 1) / BN), 1);
+            dgemm_kernel<<<grid, NTHR, 0, s>>>(false, false, rows, (int)nc, kk, 1.0, L + (long long)r0 * m, m, A + c0,
+                                               ld, 0.0, A + (long long)r0 * ld + c0, ld, false);
+            DF_CHECK_LAUNCH();
+        }
     }
 }
 

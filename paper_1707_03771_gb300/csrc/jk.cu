@@ -230,6 +230,16 @@ namespace dfhf {
 // The Coulomb build with every scratch buffer supplied by the caller and no split of the auxiliary
 // sum: Dw and Jp hold `row` doubles each, gamma `naux`. Each scratch element is written before it
 // is read within the call, so nothing has to start at zero. No allocation, no synchronisation.
+// Loads the Coulomb kernels on the current device now (under lazy module loading they would otherwise be
+// loaded, and their code placed in device memory, at their first launch)
+void coulomb_kernels_load() {
+    cudaFuncAttributes a;
+    DF_CUDA(cudaFuncGetAttributes(&a, pack_density_kernel));
+    DF_CUDA(cudaFuncGetAttributes(&a, gamma_kernel));
+    DF_CUDA(cudaFuncGetAttributes(&a, coulomb_kernel));
+    DF_CUDA(cudaFuncGetAttributes(&a, unpack_kernel));
+}
+
 void coulomb_with_scratch(cudaStream_t s, const double* B, const Packing& pk, int naux, int n, const double* dD,
                           double* dJ, double* Dw, double* gamma, double* Jp) {
     pack_density_kernel<<<dim3(pk.nt, pk.nt), 256, 0, s>>>(dD, n, Dw);

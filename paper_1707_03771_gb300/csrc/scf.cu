@@ -22,7 +22,7 @@ namespace dfhf {
 
 void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
                  int slices);
-void build_B(df_handle* h, double tau, bool keep);
+void build_B(df_handle* h, double tau, bool keep, int whitening);
 void exchange_only(df_handle* h, const double* dC, int m, int precision, int slices, double* dK);
 
 namespace {
@@ -262,7 +262,8 @@ class ScfRun {
         r_->e_nuc = h_->e_nuc;
         if (!h_->built) {
             const auto t0 = clk::now();
-            build_B(h_, o_.screen_tau, false);
+            // FP64 precision: every step FP64, the whitening included; split: the tensor-core whitening
+            build_B(h_, o_.screen_tau, false, o_.precision == DF_PREC_FP64 ? DF_WHITEN_FP64 : DF_WHITEN_SPLIT);
             r_->t_build_s = std::chrono::duration<double>(clk::now() - t0).count();
         }
         n_ = h_->n;
@@ -484,15 +485,11 @@ class ScfRun {
   private:
     using clk = std::chrono::steady_clock;
 
-    // SCF algebra products: FP64 in FP64 mode; float-float on the FP32 pipes in split mode (~2^-48 per
-    // product, far below the 1e-7 commutator threshold; at convergence the energy is stationary in the
-    // orbitals, so their rounding enters it at second order)
+    // SCF algebra products (X^T F X, the DIIS error, the orbital and density products, the approximate
+    // diagonalisation) are FP64 in both precision modes: only the exchange contraction is split
     void mm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
             const double* B, int ldb, double beta, double* C, int ldc) {
-        if (o_.precision == DF_PREC_SPLIT)
-            gemm_ff(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-        else
-            dgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        dgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     }
 
     // the full build just enqueued becomes the reference: K_ref = K, C_ref = C_occ

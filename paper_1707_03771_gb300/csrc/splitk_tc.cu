@@ -13,7 +13,8 @@
 //   * four epilogue warps (one per 32 TMEM lanes) read the level sums with tcgen05.ld, scale them by the
 //     exact power of two 2^{e_row + e_col - 7 (L + 2)} and add them into per-thread float-float rows.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records DF_E_TIMEOUT in a flag,
-// releases its tensor memory and returns.
+// waits (with the full budget) for the copies and MMAs it has already issued, releases its tensor memory and
+// returns.
 //
 // A third mode runs the metric whitening B = L^-1 A (paper eq. 1, third form) the same way with 7 slices:
 // A operand = slices of L^-1 rows (one exponent per auxiliary row), B operand = slices of the
@@ -24,6 +25,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -72,11 +74,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false (and the error flag set) if the barrier did not complete within the budget
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+// bounded pipeline wait: false (and the error flag set) if the barrier did not complete within `budget`
+// cycles (WAIT_CYCLES unless the host shortened it). The waits that drain copies and MMAs already issued,
+// before the CTA leaves, always keep the full WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err, long long budget) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_CYCLES || *(volatile int*)err) {
+        if (clock64() - t0 > budget || *(volatile int*)err) {
             atomicExch(err, DF_E_TIMEOUT);
             return false;
         }
@@ -163,6 +167,7 @@ struct TcArgs {
     int ncols;
     double* outd;
     long long ldo;
+    long long wait_cycles;   // budget of the pipeline waits (WAIT_CYCLES by default)
 };
 
 template <int S, int N, int MODE>
@@ -191,6 +196,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* err = args.err;
+    const long long wait = args.wait_cycles;
 
     // ---- work decode -------------------------------------------------------------------------
     int P = 0, m0 = 0, n0 = 0, split = 0;
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 const int kx = MODE == 1 ? (ks % kpp) * KS : ks * KS;
                 const int Pr = MODE == 1 ? p0 + ks / kpp : 0;
                 const int bs = ks & 1;
-                if (!mbar_wait(&b_empty[bs], ((ks >> 1) & 1) ^ 1, err)) break;
+                if (!mbar_wait(&b_empty[bs], ((ks >> 1) & 1) ^ 1, err, wait)) break;
                 mbar_expect_tx(&b_full[bs], BSET);
                 for (int t = 0; t < S; ++t) {
                     const int zb = MODE == 1 ? t * args.naux + Pr : t;
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 bool ok = true;
                 for (int s = 0; s < S; ++s) {
                     const int it = ks * S + s, slot = it % NA;
-                    if (!mbar_wait(&a_empty[slot], ((it / NA) & 1) ^ 1, err)) {
+                    if (!mbar_wait(&a_empty[slot], ((it / NA) & 1) ^ 1, err, wait)) {
                         ok = false;
                         break;
                     }
@@ -292,17 +298,18 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 }
                 if (!ok) break;
             }
-            // copies in flight complete before the kernel may leave: wait (bounded) for the last ones
-            if (*(volatile int*)err) {
-                for (int it = max(0, a_issued - NA); it < a_issued; ++it) {
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(&a_full[it % NA], (it / NA) & 1) && clock64() - t0 < WAIT_CYCLES) {
-                    }
+            // copies in flight complete before the kernel may leave: wait (bounded) for the last ones of every
+            // slot. After a normal run the MMA issuer has consumed them all and these waits return at once;
+            // after a timeout (here or in the issuer, which may give up while this thread has finished its
+            // loop) they keep the CTA until its copies have landed.
+            for (int it = max(0, a_issued - NA); it < a_issued; ++it) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&a_full[it % NA], (it / NA) & 1) && clock64() - t0 < WAIT_CYCLES) {
                 }
-                for (int k = max(0, b_issued - 2); k < b_issued; ++k) {
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(&b_full[k & 1], (k >> 1) & 1) && clock64() - t0 < WAIT_CYCLES) {
-                    }
+            }
+            for (int k = max(0, b_issued - 2); k < b_issued; ++k) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&b_full[k & 1], (k >> 1) & 1) && clock64() - t0 < WAIT_CYCLES) {
                 }
             }
         }
@@ -315,13 +322,13 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 const int c = chunk_of(ks);
                 if (c != chunk) {                 // new chunk: hand the finished sums to the epilogue
                     mma_commit(acc_full);
-                    ok = mbar_wait(acc_empty, (chunk & 1), err);
+                    ok = mbar_wait(acc_empty, (chunk & 1), err, wait);
                     fence_after();
                     chunk = c;
                     if (!ok) break;
                 }
                 const int bs = ks & 1;
-                if (!mbar_wait(&b_full[bs], (ks >> 1) & 1, err)) {
+                if (!mbar_wait(&b_full[bs], (ks >> 1) & 1, err, wait)) {
                     ok = false;
                     break;
                 }
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 unsigned char* bset = bbuf + bs * BSET;
                 for (int s = 0; s < S; ++s) {
                     const int it = ks * S + s, slot = it % NA;
-                    if (!mbar_wait(&a_full[slot], (it / NA) & 1, err)) {
+                    if (!mbar_wait(&a_full[slot], (it / NA) & 1, err, wait)) {
                         ok = false;
                         break;
                     }
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 blk = p0 / args.PB + ch;
                 erow = (grow < args.np) ? args.row_e[blk * args.np + grow] : 0;
             }
-            if (!mbar_wait(acc_full, ch & 1, err)) break;
+            if (!mbar_wait(acc_full, ch & 1, err, wait)) break;
             fence_after();
             // per element the levels are added in descending order; column exponents (MODE 1) are read
             // per 16-column group to keep them out of the register file
@@ -474,9 +481,19 @@ CUtensorMap make_map(const bf16* base, unsigned long long d0, unsigned long long
     return m;
 }
 
+// Budget of the kernels' pipeline waits: WAIT_CYCLES, or DFHF_TC_WAIT_CYCLES (a test knob that makes the
+// waits run out, to exercise the DF_E_TIMEOUT path; the drains of work already issued keep WAIT_CYCLES)
+long long pipeline_wait_cycles() {
+    const char* v = std::getenv("DFHF_TC_WAIT_CYCLES");
+    const long long c = v ? std::atoll(v) : 0;
+    return (c > 0 && c < WAIT_CYCLES) ? c : WAIT_CYCLES;
+}
+
 template <int S, int N, int MODE>
-void launch_tc(cudaStream_t s, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, unsigned grid) {
+void launch_tc(cudaStream_t s, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args_in, unsigned grid) {
     const size_t smem = tc_smem_bytes<S, N>();
+    TcArgs args = args_in;
+    args.wait_cycles = pipeline_wait_cycles();
     DF_CUDA(cudaFuncSetAttribute(ozaki_tc_kernel<S, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ozaki_tc_kernel<S, N, MODE><<<grid, 192, smem, s>>>(a, b, args);
     DF_CHECK_LAUNCH();

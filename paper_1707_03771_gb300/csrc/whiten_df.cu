@@ -120,105 +120,7 @@ __global__ void from_float_float_kernel(double* __restrict__ x, long long n) {
     x[i] = (double)v.x + (double)v.y;
 }
 
-// General C = alpha op(A) op(B) + beta C (row-major, FP64 in and out) in float-float arithmetic on the
-// FP32 pipes: operands are split into (hi, lo) floats as they are staged, products and sums as in the
-// whitening above (~2^-48 relative per product).
-__device__ __forceinline__ float2 split_ff(double v) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (double)hi));
-}
-
-template <bool ta, bool tb>
-__global__ void __launch_bounds__(NT) gemm_ff_kernel(int m, int n, int k, double alpha,
-                                                     const double* __restrict__ A, int lda,
-                                                     const double* __restrict__ B, int ldb, double beta,
-                                                     double* __restrict__ C, int ldc) {
-    __shared__ float2 As[2][BK][BM];
-    __shared__ float2 Bs[2][BK][BN];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    float sh[8][8], sl[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) sh[i][j] = sl[i][j] = 0.f;
-    float2 ra[4], rb[4];
-    auto fetch = [&](int k0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + q * NT;
-            const int r = ta ? idx % BM : idx / BK, c = ta ? idx / BM : idx % BK;   // op(A)[m0 + r][k0 + c]
-            const int gm = m0 + r, gk = k0 + c;
-            double va = 0.0;
-            if (gm < m && gk < k) va = ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-            ra[q] = split_ff(va);
-            const int rr = tb ? idx % BK : idx / BN, cc = tb ? idx / BK : idx % BN;  // op(B)[k0 + rr][n0 + cc]
-            const int gk2 = k0 + rr, gn = n0 + cc;
-            double vb = 0.0;
-            if (gk2 < k && gn < n) vb = tb ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn];
-            rb[q] = split_ff(vb);
-        }
-    };
-    auto store = [&](int buf) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + q * NT;
-            const int r = ta ? idx % BM : idx / BK, c = ta ? idx / BM : idx % BK;
-            As[buf][c][r] = ra[q];
-            const int rr = tb ? idx % BK : idx / BN, cc = tb ? idx / BK : idx % BN;
-            Bs[buf][rr][cc] = rb[q];
-        }
-    };
-    fetch(0);
-    store(0);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < k; k0 += BK) {
-        const bool more = k0 + BK < k;
-        if (more) fetch(k0 + BK);
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float2 a[8], b[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = As[buf][kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) df_fma(sh[i][j], sl[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
-        }
-        if (more) store(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int gm = m0 + ty + 16 * i;
-        if (gm >= m) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int gn = n0 + tx + 16 * j;
-            if (gn >= n) continue;
-            double* c = C + (long long)gm * ldc + gn;
-            const double v = alpha * ((double)sh[i][j] + (double)sl[i][j]);
-            *c = (beta == 0.0) ? v : v + beta * *c;
-        }
-    }
-}
-
 }  // namespace
-
-void gemm_ff(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
-             const double* B, int ldb, double beta, double* C, int ldc) {
-    if (m <= 0 || n <= 0) return;
-    dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM);
-    if (!ta && !tb) gemm_ff_kernel<false, false><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (!ta && tb) gemm_ff_kernel<false, true><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (ta && !tb) gemm_ff_kernel<true, false><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else gemm_ff_kernel<true, true><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    DF_CHECK_LAUNCH();
-}
 
 // B = L^-1 A in float-float. Linv (m x m, FP64) is copied to Lff (m x m doubles of scratch) as float
 // pairs; A (m x ncol FP64, row stride ld) is converted to float pairs in place and, if restore_a,

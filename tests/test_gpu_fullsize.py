@@ -64,3 +64,38 @@ def test_full_size_jk_properties(big):
     # split-precision K agrees with the FP64 K
     _, Ks = h.jk(D, C, binding.DF_PREC_SPLIT, 3)
     assert np.abs(Ks - K).max() <= 2e-5 * np.abs(K).max()
+
+
+def test_full_size_jk_sampled_against_oracle(big):
+    """J and K at full size against the oracle's eqs. (1)-(3) applied to the GPU's own B, which is streamed
+    to the host in blocks of auxiliary rows: J in full (eq. 3 is a sum over rows), and K on a sampled index
+    set I (K_II = sum_{P,i} Y_P,Ii Y_P,Ii^T needs only the rows I of every B_P: eq. 2 applied to B[:, I, :]).
+    I spans the first and last functions, tile edges and the ragged tail. The split exchange runs at 5
+    slices in the tile configuration of the benchmark (the widths the autotuner picks give bitwise the same
+    K; the split over auxiliary blocks is the occupancy heuristic the benchmark uses)."""
+    binding, system, h = big
+    rng = np.random.default_rng(34)
+    n = h.n
+    C = np.linalg.qr(rng.normal(size=(n, h.nocc)))[0]
+    D = 2 * C @ C.T
+    J64, K64 = h.jk(D, C)
+    _, K5 = h.jk(D, C, binding.DF_PREC_SPLIT, 5)
+    t = h.timings()
+    print(f"split tiles: Y {t['tc_y_tile_n']:.0f}, K {t['tc_k_tile_n']:.0f}, K split {t['tc_k_split']:.0f}")
+    idx = sorted({0, 1, 63, 64, 127, 128, 511, 512, n // 2, n - 65, n - 64, n - 2, n - 1}
+                 | set(rng.choice(n, 19, replace=False).tolist()))
+    Jr = np.zeros((n, n))
+    Kr = np.zeros((len(idx), len(idx)))
+    step = 48
+    for p0 in range(0, h.naux, step):
+        Bb = h.rows(1, p0, min(step, h.naux - p0))
+        Jr += dfrhf.df_J(Bb, D)
+        Kr += dfrhf.df_K(np.ascontiguousarray(Bb[:, idx, :]), C)
+    kmax = np.abs(Kr).max()
+    dJ = np.abs(J64 - Jr).max() / np.abs(Jr).max()
+    dK64 = np.abs(K64[np.ix_(idx, idx)] - Kr).max() / kmax
+    dK5 = np.abs(K5[np.ix_(idx, idx)] - Kr).max() / kmax
+    print(f"32 waters vs oracle: J {dJ:.2e}, K FP64 {dK64:.2e}, K split S=5 {dK5:.2e} (relative to max)")
+    assert dJ <= 1e-11
+    assert dK64 <= 1e-11
+    assert dK5 <= 2.0 ** (7 - 7 * 5)

@@ -4,9 +4,10 @@ tests/golden/oracle_energies.txt by tests/golden/make_oracle_energies.py (oracle
 
 Tolerances. The even-tempered auxiliary set makes the Coulomb metric ill-conditioned (condition number
 5.5e11 at 8 waters), so the DF exchange energy moves by about 4e-9 Eh per relative 1e-15 of rounding in
-the metric. The FP64 path must agree to 1e-9 Eh at 2 waters and 1e-7 Eh at 8 waters; a metric-factor
-inverse by products with explicit inverses (residual |X L - I| of 2e-6) missed the 8-water bar by 1.5e-6 Eh.
-The split path keeps its bar of 1e-6 Eh.
+the metric. The FP64 path must agree to 1e-9 Eh at 2 waters and 5e-9 Eh at 8 waters (measured: 2.4e-11 and
+2.1e-9 Eh); a metric-factor inverse by products with explicit inverses (residual |X L - I| of 2e-6) missed
+the 8-water bar by 1.5e-6 Eh. Both whitenings are held to it: the plain FP64 path (FP64 whitening, FP64
+exchange) and the FP64 exchange on the tensor-core-whitened B. The split path keeps its bar of 1e-6 Eh.
 """
 import os
 
@@ -17,7 +18,7 @@ from paper_1707_03771_gb300 import clusters
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_energies.txt")
-TOL_FP64 = {"water2": 1e-9, "water8": 1e-7}
+TOL_FP64 = {"water2": 1e-9, "water8": 5e-9}
 
 
 def _golden():
@@ -40,11 +41,17 @@ def lib():
 @pytest.mark.parametrize("name", ["water2", "water8"])
 def test_scf_energy_matches_oracle(lib, name):
     ref = _golden()[name]
-    with lib.Handle(clusters.workload(name)) as h:
-        h.build_B()
+    system = clusters.workload(name)
+    with lib.Handle(system) as h:
+        plain = h.scf()                      # B built here with the FP64 whitening: FP64 end to end
+        assert h.timings()["whiten_ms"] > 0
+    with lib.Handle(system) as h:
+        h.build_B()                          # tensor-core whitening
         fp64 = h.scf()
         split = h.scf(precision=lib.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1)
-    assert fp64["converged"] and split["converged"]
-    print(f"{name}: FP64 {fp64['energy'] - ref:+.2e} Eh, split {split['energy'] - ref:+.2e} Eh from the oracle")
+    assert plain["converged"] and fp64["converged"] and split["converged"]
+    print(f"{name}: plain FP64 {plain['energy'] - ref:+.2e} Eh, FP64 exchange on tensor-core B "
+          f"{fp64['energy'] - ref:+.2e} Eh, split {split['energy'] - ref:+.2e} Eh from the oracle")
+    assert abs(plain["energy"] - ref) <= TOL_FP64[name]
     assert abs(fp64["energy"] - ref) <= TOL_FP64[name]
     assert abs(split["energy"] - ref) <= 1e-6

@@ -444,3 +444,27 @@ def test_mlp_oracle_gradient_central_differences():
         e[k] = h
         fd = (mlp.loss(p + e, dims, X, Y) - mlp.loss(p - e, dims, X, Y)) / (2 * h)
         assert abs(fd - g[k]) <= 1e-7 + 1e-6 * abs(g[k]), (k, fd, g[k])
+
+
+def test_mlp_oracle_forward_and_loss_hand_computed():
+    """The oracle's forward pass and loss on a 2 -> 3 (ReLU) -> 2 network whose outputs were worked out by
+    hand. Layout per layer: W (out x in, row-major), then b. Sample 1 leaves two hidden units negative (the
+    ReLU must cut them) and has a negative output (no ReLU on the output layer); sample 2 keeps every
+    hidden unit. A transposed W, a dropped bias or an activation on the last layer changes the values."""
+    from oracle import mlp
+    W1 = [[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]
+    b1 = [0.0, 1.0, -0.5]
+    W2 = [[2.0, 1.0, -1.0], [0.5, 3.0, 4.0]]
+    b2 = [0.25, -1.0]
+    params = np.array(sum(W1, []) + b1 + sum(W2, []) + b2)
+    dims = [2, 3, 2]
+    X = np.array([[1.0, -2.0], [0.5, 1.5]])
+    # sample 1: z1 = (1, -1, -1.5) -> h = (1, 0, 0) -> out = (2 + 0.25, 0.5 - 1) = (2.25, -0.5)
+    # sample 2: z1 = (0.5, 2.5, 1.5) = h -> out = (1 + 2.5 - 1.5 + 0.25, 0.25 + 7.5 + 6 - 1) = (2.25, 12.75)
+    Z, acts = mlp.forward(params, dims, X)
+    assert np.array_equal(Z[0], [[1.0, -1.0, -1.5], [0.5, 2.5, 1.5]])
+    assert np.array_equal(acts[1], [[1.0, 0.0, 0.0], [0.5, 2.5, 1.5]])
+    assert np.array_equal(acts[-1], [[2.25, -0.5], [2.25, 12.75]])
+    # loss: mean of (0.25, -0.5, 0.25, 0.75)^2 = 0.9375 / 4
+    Y = np.array([[2.0, 0.0], [2.0, 12.0]])
+    assert mlp.loss(params, dims, X, Y) == 0.234375

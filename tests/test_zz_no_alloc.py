@@ -4,7 +4,9 @@ Some callers cannot call cudaMalloc (an application that owns all device memory 
 allocator, or a loop that cannot afford an allocation's synchronisation). This entry point takes its
 scratch from a fixed array inside the library; here its J is checked against the J of the regular
 entry point df_jk, within the tolerance of the other J/K kernel tests, on two calls in a row with
-different densities (the shared scratch keeps the previous call's contents).
+different densities (the shared scratch keeps the previous call's contents), and the device's free
+memory is read before and after each call: the handle resolved the scratch array (and loaded the kernels)
+when it was created, so neither the first call nor the second may take any device memory.
 
 Collected last so that a run stopping at its first failure has already run every other test.
 """
@@ -39,8 +41,11 @@ def test_noalloc_coulomb_matches_df_jk_twice(env, name):
             dD = torch.from_numpy(D).to(dev)
             dJ = torch.full((h.n, h.n), float("nan"), dtype=torch.float64, device=dev)
             torch.cuda.synchronize()          # D is on the device before the library's stream reads it
+            free_before = torch.cuda.mem_get_info(dev)[0]
             h.coulomb_noalloc(dD.data_ptr(), dJ.data_ptr())
             torch.cuda.synchronize()          # the call only enqueues work
+            free_after = torch.cuda.mem_get_info(dev)[0]
+            assert free_after == free_before, (name, call, free_before - free_after)
             J = dJ.cpu().numpy()
             assert np.all(np.isfinite(J)), (name, call)
             assert np.abs(J - J_ref).max() <= TOL * np.abs(J_ref).max(), (name, call)
