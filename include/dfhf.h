@@ -24,6 +24,12 @@
  *     df_last_error gives the detail of the last failure on that handle. No C++ exception crosses
  *     this interface.
  *   - One GPU: every call runs on the device that was current at df_init, on the handle's stream.
+ *   - Host threads: calls on one handle must not overlap (one thread at a time per handle; the handle's
+ *     buffers, stream and solver state are not locked). Calls on different handles may run concurrently
+ *     from several threads: the process-wide state (the Rys root table, the autotuner's tile choices, the
+ *     tensor-map encoder entry point) is guarded by mutexes, and each handle owns its stream, its cuSOLVER
+ *     handle and its device buffers. The one shared device buffer is df_coulomb_noalloc's scratch (see
+ *     there). scf_run_batch drives many handles from the calling thread alone.
  */
 #ifndef DFHF_H
 #define DFHF_H

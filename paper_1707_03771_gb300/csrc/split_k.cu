@@ -748,7 +748,10 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         st->nsplit_tc = ksplit;
         h->timings_ms[12] = ch.yN;
         h->timings_ms[13] = ksplit;
-        h->timings_ms[14] = g_tune_ms;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            h->timings_ms[14] = g_tune_ms;
+        }
         h->timings_ms[15] = ch.kN;
         DF_CUDA(cudaEventRecord(ev[2], s));
         k_split_tc(s, S, ch.kN, st->Ys, st->Ye, naux, np, ldy, st->PB, ksplit, st->tiles128, st->ntiles128,

@@ -468,3 +468,88 @@ def test_mlp_oracle_forward_and_loss_hand_computed():
     # loss: mean of (0.25, -0.5, 0.25, 0.75)^2 = 0.9375 / 4
     Y = np.array([[2.0, 0.0], [2.0, 12.0]])
     assert mlp.loss(params, dims, X, Y) == 0.234375
+
+
+# ---------------------------------------------------------------------------------------------
+# superposition of atomic densities (oracle/sad.py)
+# ---------------------------------------------------------------------------------------------
+
+def test_aufbau_occupations_hand_cases():
+    from oracle import sad
+    eps = np.array([-20.0, -1.0, -0.5, -0.5 + 1e-12, -0.5 - 1e-12, 0.3, 0.3, 0.9])
+    assert np.allclose(sad.aufbau_occupations(eps, 8), [2, 2, 4 / 3, 4 / 3, 4 / 3, 0, 0, 0], atol=0)
+    assert np.array_equal(sad.aufbau_occupations(eps, 1), [1, 0, 0, 0, 0, 0, 0, 0])
+    assert np.array_equal(sad.aufbau_occupations(eps, 10), [2, 2, 2, 2, 2, 0, 0, 0])
+    assert np.array_equal(sad.aufbau_occupations(eps, 11), [2, 2, 2, 2, 2, 0.5, 0.5, 0])
+    assert sad.aufbau_occupations(eps, 7).sum() == 7
+
+
+@pytest.fixture(scope="module")
+def water2_sys():
+    return clusters.workload("water2")
+
+
+@pytest.mark.parametrize("atom_index,z", [(0, 10), (1, 2)])
+def test_fractional_scf_reduces_to_rhf_for_closed_shells(water2_sys, atom_index, z):
+    """With every occupied shell full (Ne in the oxygen shells, He in the hydrogen shells) the occupations
+    are integers and the fractional-occupation SCF is the closed-shell DF-RHF of dfrhf.scf: same energy."""
+    from oracle import sad
+    atom = sad.atom_system(water2_sys, atom_index)
+    atom.atoms["Z"] = z
+    D, e, eps, occ, _ = sad.atomic_scf(atom)
+    ref = dfrhf.scf(atom)
+    assert np.array_equal(occ[:z // 2], np.full(z // 2, 2.0)) and occ[z // 2:].sum() == 0
+    assert abs(e - ref.energy) <= 1e-9, (e, ref.energy)
+    assert np.abs(D - ref.D).max() <= 1e-6
+
+
+def test_oxygen_atom_density_is_spherical(water2_sys):
+    """Fractional occupation 4/3 of each 2p orbital: tr(DS) = 8, and the density is spherical, i.e. in
+    real solid harmonics every (l, l') block between two shells is zero for l != l' and a multiple of the
+    identity over m for l = l' (the rotation matrices of each l are orthogonal)."""
+    from oracle import sad
+    atom = sad.atom_system(water2_sys, 0)
+    D, e, eps, occ, _ = sad.atomic_scf(atom)
+    S = dfrhf.overlap(atom)
+    assert abs(np.sum(D * S) - 8.0) <= 1e-11
+    assert np.allclose(occ[:5], [2, 2, 4 / 3, 4 / 3, 4 / 3], rtol=0, atol=1e-15) and occ[5:].sum() == 0
+    ls = atom.basis["l"]
+    off = np.concatenate([[0], np.cumsum(2 * ls + 1)])
+    scale = np.abs(D).max()
+    for i, li in enumerate(ls):
+        for j, lj in enumerate(ls):
+            blk = D[off[i]:off[i + 1], off[j]:off[j + 1]]
+            if li != lj:
+                assert np.abs(blk).max() <= 1e-10 * scale
+            else:
+                assert np.abs(blk - blk[0, 0] * np.eye(2 * li + 1)).max() <= 1e-10 * scale
+
+
+def test_hydrogen_atom_density_is_one_electron(water2_sys):
+    from oracle import sad
+    atom = sad.atom_system(water2_sys, 1)
+    D, e, eps, occ, _ = sad.atomic_scf(atom)
+    S = dfrhf.overlap(atom)
+    assert occ[0] == 1.0 and occ[1:].sum() == 0
+    w = np.sort(np.linalg.eigvals(D @ S).real)
+    assert abs(w[-1] - 1.0) <= 1e-10 and np.abs(w[:-1]).max() <= 1e-10   # one orbital, occupation 1
+
+
+def test_sad_density_assembly(water2_sys):
+    from oracle import sad
+    D0 = sad.sad_density(water2_sys)
+    S = dfrhf.overlap(water2_sys)
+    assert abs(np.sum(D0 * S) - water2_sys.n_electrons) <= 1e-10
+    off = np.concatenate([[0], np.cumsum(2 * water2_sys.basis["l"] + 1)])
+    blocks = []
+    for a in range(len(water2_sys.atoms)):
+        sh = np.flatnonzero(water2_sys.basis["atom"] == a)
+        blocks.append((off[sh[0]], off[sh[-1] + 1]))
+    Dox = sad.atomic_scf(sad.atom_system(water2_sys, 0))[0]
+    for a, (lo, hi) in enumerate(blocks):
+        for b, (lo2, hi2) in enumerate(blocks):
+            blk = D0[lo:hi, lo2:hi2]
+            if a != b:
+                assert not blk.any()
+        if int(water2_sys.atoms["Z"][a]) == 8:
+            assert np.abs(D0[lo:hi, lo:hi] - Dox).max() <= 1e-12
