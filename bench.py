@@ -143,19 +143,30 @@ def _scf_info(res):
             "incremental_builds": res["incremental_builds"], "approx_steps": res["approx_steps"]}
 
 
-def fp64_peak(binding, gpu_index):
-    """The FP64 pipe's rate on this GPU, measured now (DFMA and FP64 mma.sync loops of about 1 s each) with
-    the SM clock sampled meanwhile: the denominator of the FP64 kernels' roofline fractions."""
+# FP64 multiply-adds per clock per SM of GB300 (its nominal 1.25 TFLOP/s dense FP64 at the 2070 MHz maximum
+# SM clock over 152 SMs is 2 multiply-adds, 4 flops, per clock per SM)
+FP64_FMA_PER_SM_CLOCK = 2
+
+
+def fp64_peak(binding, gpu_index, sm_count, sm_mhz):
+    """The FP64 pipe's peak for the roofline: unit count x SMs x the SM clock sampled during the timed J/K
+    builds (flops = 2 x multiply-adds). Beside it, two loops measured now with the clock sampled meanwhile:
+    DFMA and FP64 mma.sync (about 1 s each); they stay below the unit-count figure, which the bandwidth-free
+    FP64 kernels here (gamma and coulomb) come within a few per cent of."""
     with ClockSampler(gpu_index) as clk:
         dfma, ms_a = binding.fp64_rate(0, 480000)
         dmma, ms_b = binding.fp64_rate(1, 120000)
     c = clk.summary()
-    out = {"dfma_tflops": dfma, "dmma_tflops": dmma, "peak_tflops": max(dfma, dmma),
-           "timed_ms": [ms_a, ms_b], "clocks": c,
+    peak = 2.0 * FP64_FMA_PER_SM_CLOCK * sm_count * (sm_mhz or 2070.0) * 1e6 / 1e12
+    out = {"peak_tflops": peak,
+           "peak_source": f"{FP64_FMA_PER_SM_CLOCK} FP64 multiply-adds per clock per SM x {sm_count} SMs x "
+                          f"{sm_mhz or 2070.0:.0f} MHz (median SM clock of the timed builds)",
+           "measured_dfma_tflops": dfma, "measured_dmma_tflops": dmma, "measured_ms": [ms_a, ms_b],
+           "measured_clocks": c,
            "how": "df_fp64_rate: 4 CTAs x 256 threads per SM; DFMA 8 independent chains per thread, "
                   "DMMA 4 independent m8n8k4 accumulations per warp; 2 flops per multiply-add"}
     if c.get("sm_mhz"):
-        out["fp64_flops_per_sm_per_clock"] = max(dfma, dmma) * 1e12 / (152 * c["sm_mhz"] * 1e6)
+        out["measured_fp64_flops_per_sm_per_clock"] = max(dfma, dmma) * 1e12 / (sm_count * c["sm_mhz"] * 1e6)
     return out
 
 
@@ -262,7 +273,13 @@ def gpu_arm(args):
         # split precision: S = 3 early, then a 5-slice reference K every 8 iterations with 3-slice
         # density-change builds in between (incremental Fock); "_full" keeps full 5-slice builds
         inc = 1 if split else 0
-        runs = [("split" if split else "fp64", prec, None, inc)]
+        runs = [("split" if split else "fp64", prec, None, inc),
+                ("split_sad" if split else "fp64_sad", prec, "sad", inc)]
+        if split:
+            # the SAD start builds its first exchange from the atoms' occupied orbitals (7 per water): the
+            # autotuner's one-time choice for that width is made here, outside the timed runs
+            nw = len(system.atoms) // 3
+            h.jk(D, np.ascontiguousarray(np.concatenate([C, C[:, :7 * nw - nocc]], axis=1)), prec, 3)
         if guess_net is not None:
             t0 = time.perf_counter()
             D0 = h.mlp_guess(guess_net, bf16=True)
@@ -272,9 +289,10 @@ def gpu_arm(args):
             if split:
                 runs.append(("split_learned_full", prec, (D0, t_guess), 0))
         for label, p, g, inc_ in runs:
-            res = h.scf(precision=p, slices=3, incremental=inc_, approx_diag=inc_, guess=None if g is None else g[0])
+            res = h.scf(precision=p, slices=3, incremental=inc_, approx_diag=inc_,
+                        guess=g if g is None or isinstance(g, str) else g[0])
             hist[label] = h.history()[:, 1]
-            ttc[label] = t_build + res["t_total_s"] + (0.0 if g is None else g[1])
+            ttc[label] = t_build + res["t_total_s"] + (g[1] if isinstance(g, tuple) else 0.0)
             scf_info[label] = _scf_info(res)
 
     peaks, peak_src = _peaks()
@@ -318,7 +336,9 @@ def gpu_arm(args):
     if guess_net is not None:
         guess_net.close()
 
-    fp64pk = fp64_peak(binding, local)
+    clk_summary = clocks.summary()
+    fp64pk = fp64_peak(binding, local, torch.cuda.get_device_properties(dev).multi_processor_count,
+                       clk_summary.get("sm_mhz"))
     fp64_peak_tf = fp64pk["peak_tflops"]
     alg_k_flops = 2.0 * naux * n * n * nocc + 1.0 * naux * n * n * nocc   # Y = B C and K = sum Y Y^T
     if not split:
@@ -326,7 +346,7 @@ def gpu_arm(args):
         achieved = flops / (avg["ytransform_ms"] * 1e-3) / 1e12
         roofline = {"kernel": "y_transform_kernel (FP64 DFMA)", "bound": "alu", "achieved": achieved,
                     "peak": fp64_peak_tf, "unit": "TFLOP/s", "frac": achieved / fp64_peak_tf,
-                    "peak_source": "FP64 rate measured in this run (fp64_peak)", "traffic": None}
+                    "peak_source": fp64pk["peak_source"], "traffic": None}
     else:
         npad = (n + 63) // 64 * 64
         ldy = (nocc + 31) // 32 * 32
@@ -457,6 +477,12 @@ def c2_measure(args, binding, clusters, lib, dev, stream, guess_net):
         res = h.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1)
         out["ttc_split_s"] = t_build + res["t_total_s"]
         out["scf_split"] = _scf_info(res)
+        nw = len(system.atoms) // 3
+        h.jk(D, np.ascontiguousarray(np.concatenate([C, C[:, :7 * nw - h.nocc]], axis=1)), binding.DF_PREC_SPLIT, 3)
+        res_s = h.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1, guess="sad")
+        out["ttc_split_sad_s"] = t_build + res_s["t_total_s"]
+        out["scf_split_sad"] = _scf_info(res_s)
+        out["dE_sad_vs_core"] = res_s["energy"] - res["energy"]
         if guess_net is not None:
             t1 = time.perf_counter()
             D0 = h.mlp_guess(guess_net, bf16=True)
@@ -525,24 +551,33 @@ def guess_study(args):
     for w, seed in evals:
         with binding.Handle(clusters.water_cluster(w, seed)) as h:
             h.build_B()
-            core = h.scf(precision=prec, slices=3, incremental=1)
+            core = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1)
+            sadr = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess="sad")
             t0 = time.perf_counter()
             D0 = h.mlp_guess(net, bf16=True)
             t_guess = time.perf_counter() - t0
-            lrn = h.scf(precision=prec, slices=3, incremental=1, guess=D0)
+            lrn = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess=D0)
         rows.append({"waters": w, "seed": seed, "iterations_core": core["iterations"],
-                     "iterations_learned": lrn["iterations"], "t_scf_core_s": core["t_total_s"],
+                     "iterations_sad": sadr["iterations"], "iterations_learned": lrn["iterations"],
+                     "t_scf_core_s": core["t_total_s"], "t_scf_sad_s": sadr["t_total_s"],
                      "t_scf_learned_s": lrn["t_total_s"] + t_guess,
                      "dE_learned_vs_core": lrn["energy"] - core["energy"],
-                     "converged": bool(core["converged"] and lrn["converged"])})
+                     "dE_sad_vs_core": sadr["energy"] - core["energy"],
+                     "converged": bool(core["converged"] and lrn["converged"] and sadr["converged"])})
     net.close()
     it_c = [r["iterations_core"] for r in rows]
+    it_s = [r["iterations_sad"] for r in rows]
     it_l = [r["iterations_learned"] for r in rows]
     print(json.dumps({"study": "learned initial guess on held-out clusters", "training": summary,
                       "eval_clusters": n_eval, "mean_iterations_core": float(np.mean(it_c)),
+                      "mean_iterations_sad": float(np.mean(it_s)),
                       "mean_iterations_learned": float(np.mean(it_l)),
-                      "iterations_saved_fraction": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
+                      "iterations_saved_vs_core": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
+                      "iterations_saved_vs_sad": 1.0 - float(np.sum(it_l)) / float(np.sum(it_s)),
+                      "time_saved_vs_sad": 1.0 - float(sum(r["t_scf_learned_s"] for r in rows))
+                                           / float(sum(r["t_scf_sad_s"] for r in rows)),
                       "max_abs_dE_learned_vs_core": float(max(abs(r["dE_learned_vs_core"]) for r in rows)),
+                      "max_abs_dE_sad_vs_core": float(max(abs(r["dE_sad_vs_core"]) for r in rows)),
                       "all_converged": all(r["converged"] for r in rows), "clusters": rows}))
 
 

@@ -63,13 +63,16 @@ typedef struct { int atom; int l; double exponent; double center[3]; } df_shell;
 #define DF_PREC_SPLIT 1      /* K from split BF16 slices on tensor cores, exact FP32 chunk sums, float-float sum */
 
 #define DF_GUESS_CORE 0      /* core-Hamiltonian guess */
+#define DF_GUESS_SAD 1       /* superposition of atomic densities (df_sad_density): the first Fock matrix is
+                                built from that density itself */
 
 typedef struct {
     double conv_E;           /* |E_n - E_{n-1}| threshold (hartree), e.g. 1e-10 */
     double conv_err;         /* max |X^T (F D S - S D F) X| threshold, e.g. 1e-7 */
     int max_iter;            /* iteration cap */
     int diis_size;           /* Pulay subspace (<= 16) */
-    int guess;               /* DF_GUESS_* */
+    int guess;               /* DF_GUESS_CORE or DF_GUESS_SAD (else DF_E_ARG); scf_run_guess's D0 takes
+                                precedence */
     int precision;           /* DF_PREC_* */
     int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..5) in early iterations;
                                 once max|e| < 1e-4 the exchange is built with 5 slices, and the SCF
@@ -150,7 +153,7 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
           int device_ptrs, int precision, int slices);   /* slices: 2..5 for DF_PREC_SPLIT */
 
 /* Full RHF SCF (paper, section "Standard algorithms": the Fock builder uses density fitting) from the
- * core-Hamiltonian guess; builds B first if needed (screen_tau from opts; DF_WHITEN_FP64 for
+ * guess options.guess names; builds B first if needed (screen_tau from opts; DF_WHITEN_FP64 for
  * DF_PREC_FP64, DF_WHITEN_SPLIT for DF_PREC_SPLIT).
  * Results in *out; returns out->status. */
 int scf_run(df_handle* h, const df_options* opts, df_result* out);
@@ -162,6 +165,17 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out);
  * first for handles that lack it. out[i] receives molecule i's result; the return value is DF_OK if all
  * converged, else the first failing status. */
 int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out);
+
+/* Superposition of atomic densities (the initial guess the SCF takes with options.guess = DF_GUESS_SAD; the
+ * paper names no guess): every element gets a spherically averaged, fractional-occupation restricted
+ * DF-HF of the neutral atom in the shells the molecule assigns to that atom (df_shell.atom, which must name
+ * the atom for this guess): Aufbau occupations in which degenerate orbitals share their electrons equally,
+ * F = H + J[D] - K with K the exchange of the occupied orbitals weighted by sqrt(n_i / 2), converged to
+ * |dE| < 1e-11 Eh and max|X^T(FDS - SDF)X| < 1e-9 on the GPU. D0 (host, n x n) receives the block-diagonal
+ * assembly of the atoms' densities, scaled to tr(D0 S) = N electrons. Atomic results are kept for the
+ * process per element and shell set. DF_E_ARG if an atom with orbital shells has no auxiliary shells;
+ * DF_E_NUMERIC if an atomic SCF does not converge. */
+int df_sad_density(df_handle* h, double* D0);
 
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
  * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric

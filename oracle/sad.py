@@ -51,10 +51,12 @@ def atom_system(sys, a: int):
     return replace(sys, atoms=atoms, basis=basis, aux=aux, charge=0, label=f"atom{a}")
 
 
-def atomic_scf(atom, nelec: float | None = None, conv_E: float = 1e-10, conv_err: float = 1e-7,
+def atomic_scf(atom, nelec: float | None = None, conv_E: float = 1e-11, conv_err: float = 1e-9,
                max_iter: int = 200, diis_size: int = 8):
     """Fractional-occupation restricted DF-HF of one atom (or any system): returns (D, energy, eps, occ,
-    iterations). Core-Hamiltonian start, Pulay DIIS on X^T (F D S - S D F) X as in dfrhf.scf."""
+    iterations). Core-Hamiltonian start, Pulay DIIS on X^T (F D S - S D F) X as in dfrhf.scf; converged to
+    |dE| < 1e-11 Eh and max|e| < 1e-9 (tighter than the molecular SCF: the guess should not carry the
+    atoms' convergence noise)."""
     if nelec is None:
         nelec = float(atom.atoms["Z"].sum())
     S = dfrhf.overlap(atom)

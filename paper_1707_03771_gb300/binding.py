@@ -15,13 +15,14 @@ from . import build as _build
 DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, DF_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 DF_WHITEN_SPLIT, DF_WHITEN_FP64 = 0, 1
+DF_GUESS_CORE, DF_GUESS_SAD = 0, 1
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
             "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
-            "df_fp64_rate"]
+            "df_fp64_rate", "df_sad_density"]
 DF_MLP_NFEAT = 57
 
 
@@ -83,6 +84,7 @@ def load(path: str | None = None):
     L.df_rint_pow2.argtypes = [dp, P(c_int), ctypes.c_longlong, P(ctypes.c_longlong)]
     L.df_prepare.argtypes = []
     L.df_fp64_rate.argtypes = [c_int, ctypes.c_longlong, dp, dp]
+    L.df_sad_density.argtypes = [c_void_p, dp]
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
@@ -194,10 +196,15 @@ class Handle:
 
     def scf(self, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
             incremental=0, screen_tau=0.0, guess=None, approx_diag=0):
-        """SCF from the core-Hamiltonian guess, or from the natural orbitals of `guess` (n x n)."""
-        o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau, approx_diag)
+        """SCF from the core-Hamiltonian guess, from the superposition of atomic densities (guess="sad"), or
+        from the natural orbitals of a guess density (guess: an n x n array)."""
+        sad = isinstance(guess, str)
+        if sad and guess != "sad":
+            raise ValueError("guess: None, 'sad' or an n x n density")
+        o = Options(conv_E, conv_err, max_iter, diis_size, DF_GUESS_SAD if sad else DF_GUESS_CORE, precision, slices,
+                    incremental, screen_tau, approx_diag)
         r = Result()
-        if guess is None:
+        if guess is None or sad:
             rc = load().scf_run(self.h, ctypes.byref(o), ctypes.byref(r))
         else:
             g = np.ascontiguousarray(guess, dtype=np.float64)
@@ -223,6 +230,12 @@ class Handle:
     def mlp_guess(self, mlp, bf16=True):
         D0 = np.empty((self.n, self.n))
         self._check(load().df_mlp_guess(self.h, mlp.m, int(bf16), _dp(D0)), "df_mlp_guess")
+        return D0
+
+    def sad_density(self):
+        """The superposition-of-atomic-densities guess density (n x n), df_sad_density."""
+        D0 = np.empty((self.n, self.n))
+        self._check(load().df_sad_density(self.h, _dp(D0)), "df_sad_density")
         return D0
 
     def history(self):
@@ -278,11 +291,15 @@ class Handle:
 
 
 def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, precision=DF_PREC_FP64, slices=3,
-              screen_tau=0.0, incremental=0, approx_diag=0):
-    """Solve several molecules together (scf_run_batch); returns one result dict per handle."""
+              screen_tau=0.0, incremental=0, approx_diag=0, guess=None):
+    """Solve several molecules together (scf_run_batch); guess None (core Hamiltonian) or "sad". Returns one
+    result dict per handle."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[hd.h.value for hd in handles])
-    o = Options(conv_E, conv_err, max_iter, diis_size, 0, precision, slices, incremental, screen_tau, approx_diag)
+    if guess not in (None, "sad"):
+        raise ValueError("guess: None or 'sad'")
+    o = Options(conv_E, conv_err, max_iter, diis_size, DF_GUESS_SAD if guess == "sad" else DF_GUESS_CORE, precision,
+                slices, incremental, screen_tau, approx_diag)
     out = (Result * n)()
     rc = load().scf_run_batch(hs, n, ctypes.byref(o), out)
     if rc not in (DF_OK, DF_E_NOTCONV):

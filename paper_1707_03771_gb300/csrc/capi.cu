@@ -351,6 +351,16 @@ const char* df_last_error(const df_handle* h) { return h ? h->last_error.c_str()
 
 int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh, const df_shell* aux, int naux_sh,
             int charge, df_handle** out) {
+    return dfhf::init_handle(atoms, natom, basis, nbasis_sh, aux, naux_sh, charge, out, true);
+}
+
+}  // extern "C"
+
+// A handle for the system; closed_shell = false admits any electron count >= 1 (the atoms of the
+// superposition-of-atomic-densities guess, whose SCF takes fractional occupations), with nocc the number
+// of orbitals an Aufbau filling would touch, ceil(N / 2)
+int dfhf::init_handle(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh, const df_shell* aux,
+                      int naux_sh, int charge, df_handle** out, bool closed_shell) {
     if (!out) return DF_E_ARG;
     *out = nullptr;
     if (!atoms || !basis || !aux || natom < 1 || nbasis_sh < 1 || naux_sh < 1) return DF_E_ARG;
@@ -364,7 +374,7 @@ int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_s
         zsum += atoms[i].Z;
     }
     const int nelec = zsum - charge;
-    if (nelec < 2 || nelec % 2) return DF_E_ARG;
+    if (closed_shell ? (nelec < 2 || nelec % 2) : nelec < 1) return DF_E_ARG;
     df_handle* h = new (std::nothrow) df_handle();
     if (!h) return DF_E_NOMEM;
     try {
@@ -384,7 +394,7 @@ int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_s
         for (auto& s : h->basis) h->n += 2 * s.l + 1;
         for (auto& s : h->aux) h->naux += 2 * s.l + 1;
         h->nelec = nelec;
-        h->nocc = nelec / 2;
+        h->nocc = (nelec + 1) / 2;
         if (h->nocc > h->n) throw Error{DF_E_ARG, "more occupied orbitals than basis functions"};
         for (int i = 0; i < natom; ++i)
             for (int j = 0; j < i; ++j) {
@@ -452,6 +462,8 @@ int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_s
     return DF_OK;
 }
 
+extern "C" {
+
 int df_sizes(const df_handle* h, int* n, int* naux, int* nocc, long long* packed_row) {
     if (!h) return DF_E_ARG;
     if (n) *n = h->n;
@@ -516,7 +528,8 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
 int scf_run(df_handle* h, const df_options* opts, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
-        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
+        (opts->approx_diag != 0 && opts->approx_diag != 1) ||
+        (opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SAD)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     try {
@@ -531,7 +544,8 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out) {
 int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
-        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
+        (opts->approx_diag != 0 && opts->approx_diag != 1) ||
+        (opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SAD)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     try {
@@ -546,7 +560,8 @@ int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_res
 int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* out) {
     if (!hs || nmol < 1 || !opts || !out) return DF_E_ARG;
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
-        (opts->approx_diag != 0 && opts->approx_diag != 1)) return DF_E_ARG;
+        (opts->approx_diag != 0 && opts->approx_diag != 1) ||
+        (opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SAD)) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
     int dev = -1;

@@ -174,6 +174,10 @@ struct df_handle {
 };
 
 namespace dfhf {
+// handle creation (capi.cu); closed_shell = false admits any electron count (atoms of the SAD guess)
+int init_handle(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh, const df_shell* aux,
+                int naux_sh, int charge, df_handle** out, bool closed_shell);
+
 // integral builders (integrals.cu)
 void compute_one_electron(df_handle* h);
 void compute_metric(df_handle* h);
@@ -208,6 +212,11 @@ int noalloc_scratch_address(double** out, std::string* why);
 
 // SCF (scf.cu)
 int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess = nullptr);
+void atomic_scf(df_handle* ha, double nelec, std::vector<double>& Cw, int& m);
+std::vector<double> aufbau_occupations(const std::vector<double>& eps, double nelec);
+
+// superposition of atomic densities (sad.cu): C0 (device, n x m0) with D0 = 2 C0 C0^T
+void sad_factor(df_handle* h, DevBuf<double>& C0, int& m0);
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);

@@ -244,7 +244,37 @@ __global__ void invsqrt_series_kernel(double* __restrict__ M, const double* __re
     M[idx] = (idx / m == idx % m ? 1.875 : 0.0) - 1.25 * M[idx] + 0.375 * M2[idx];
 }
 
+// Vw[i][k] = V[i][k] w[i] for the first m rows (the occupied eigenvectors weighted by sqrt(n_i / 2))
+__global__ void weight_rows_kernel(const double* __restrict__ V, const double* __restrict__ w, int m, int len,
+                                   double* __restrict__ Vw) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * len) return;
+    Vw[idx] = V[idx] * w[idx / len];
+}
+
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// Occupations of orbitals with ascending energies eps: Aufbau in which a set of degenerate orbitals
+// (energies within 1e-6 max(1, |eps|) of the set's first; a shell of l > 0 of a spherical atom) takes the
+// electrons that reach it in equal shares of at most 2.
+std::vector<double> aufbau_occupations(const std::vector<double>& eps, double nelec) {
+    std::vector<double> occ(eps.size(), 0.0);
+    double left = nelec;
+    size_t i = 0;
+    while (left > 0 && i < eps.size()) {
+        size_t j = i + 1;
+        while (j < eps.size() && std::fabs(eps[j] - eps[i]) <= 1e-6 * std::max(1.0, std::fabs(eps[i]))) ++j;
+        const double take = std::min(left, 2.0 * (double)(j - i));
+        for (size_t k = i; k < j; ++k) occ[k] = take / (double)(j - i);
+        left -= take;
+        i = j;
+    }
+    return occ;
+}
+
+namespace {
 
 // One molecule's SCF as a sequence of asynchronous iterations with a single host synchronisation each
 // (the energy terms, max|e| and status words), so that many molecules can advance in lock-step on their
@@ -254,6 +284,21 @@ class ScfRun {
     ScfRun(df_handle* h, const df_options* o, df_result* r, const double* guess = nullptr)
         : h_(h), o_(*o), r_(r), guess_(guess) {}
     ~ScfRun() { release(); }
+
+    // fractional occupations of nelec electrons by Aufbau with degenerate sets sharing equally (the atoms of
+    // the SAD guess): the occupied rows of each Roothaan step are weighted by sqrt(n_i / 2), so that
+    // D = 2 C_w C_w^T = sum n_i C_i C_i^T and the orbital-form exchange of C_w is half the exchange of D
+    void set_fractional(double nelec) {
+        frac_ = true;
+        nelec_frac_ = nelec;
+    }
+    // the first Fock matrix from D0 = 2 C0 C0^T (C0: device, n x m, row-major), e.g. the SAD factor
+    void set_initial_factor(const double* C0, int m) {
+        C0_ = C0;
+        m0_ = m;
+    }
+    const double* occupied_factor() const { return h_->dC.p; }
+    int occupied_count() const { return nocc_; }
 
     // orthogonaliser and core-Hamiltonian guess (synchronises: the dropped-eigenvalue count is needed)
     void begin() {
@@ -308,7 +353,11 @@ class ScfRun {
         h_->C.alloc((size_t)n_ * nX_);
         DF_CUDA(cudaMemsetAsync(h_->C.p, 0, sizeof(double) * n_ * nX_, s_));
         DF_CUDA(cudaMemsetAsync(h_->eps.p, 0, sizeof(double) * n_, s_));
-        ensure_jk_buffers(h_, nocc_);
+        ensure_jk_buffers(h_, frac_ ? nX_ : std::max(nocc_, C0_ ? m0_ : 0));
+        if (frac_) {
+            DF_CUDA(cudaMalloc((void**)&vto_, sizeof(double) * ((long long)nX_ * nX_ + nX_)));
+            wocc_ = vto_ + (long long)nX_ * nX_;
+        }
         h_->diisF.alloc((size_t)DIIS_MAX * nn_);
         h_->diisE.alloc((size_t)DIIS_MAX * nX_ * nX_);
         h_->diisB.alloc(DIIS_MAX * DIIS_MAX + 8 + DIIS_MAX);   // B matrix | scalars (8) | coef
@@ -327,7 +376,12 @@ class ScfRun {
         present_.assign(DIIS_MAX, 0);
         order_.clear();
         h_->history.clear();
-        if (guess_) {
+        if (C0_) {
+            // the first Fock matrix from the factor: C_occ = C0 (m0 columns), D = 2 C0 C0^T
+            DF_CUDA(cudaMemcpyAsync(h_->dC.p, C0_, sizeof(double) * n_ * m0_, cudaMemcpyDeviceToDevice, s_));
+            mm(s_, false, true, n_, n_, m0_, 2.0, h_->dC.p, m0_, h_->dC.p, m0_, 0.0, h_->Dm.p, n_);
+            first_factor_ = true;
+        } else if (guess_) {
             natural_orbitals(guess_);
         } else {
             to_orth(h_->H.p, Fp_);   // core-Hamiltonian guess
@@ -358,7 +412,8 @@ class ScfRun {
             ++inc_since_ref_;
             ++r_->incremental_builds;
         } else {
-            jk_dispatch(h_, h_->Dm.p, h_->dC.p, nocc_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+            jk_dispatch(h_, h_->Dm.p, h_->dC.p, first_factor_ ? m0_ : nocc_, h_->dJ.p, h_->dK.p, o_.precision,
+                        slices_);
             if (o_.incremental && late_) set_reference();
         }
         DF_CUDA(cudaEventRecord(ej1_, s_));
@@ -368,8 +423,10 @@ class ScfRun {
         DF_CHECK_LAUNCH();
         // F' = X^T F X; error e = X^T (FDS - SDF) X = 2 (F' P - P F'), P = V_occ V_occ^T, into the next slot
         to_orth(h_->F.p, Fo_);
-        mm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
-        mm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
+        if (!first_factor_) {
+            mm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
+            mm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
+        }
         slot_ = 0;
         if ((int)order_.size() < dsize_) {
             while (present_[slot_]) ++slot_;
@@ -379,8 +436,17 @@ class ScfRun {
             present_[slot_] = 0;
         }
         double* Eslot = h_->diisE.p + (long long)slot_ * nX_ * nX_;
-        antisym_kernel<<<nblk((long long)nX_ * nX_), 256, 0, s_>>>(h_->work1.p, nX_, 2.0, Eslot);
-        DF_CHECK_LAUNCH();
+        if (first_factor_) {
+            // the density is the factor's, not an Aufbau projector: e = X^T (F D S - S D F) X in full
+            mm(s_, false, false, n_, n_, n_, 1.0, h_->F.p, n_, h_->Dm.p, n_, 0.0, h_->work1.p, n_);
+            mm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
+            antisym_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->work2.p, n_, 1.0, h_->work3.p);
+            DF_CHECK_LAUNCH();
+            to_orth(h_->work3.p, Eslot);
+        } else {
+            antisym_kernel<<<nblk((long long)nX_ * nX_), 256, 0, s_>>>(h_->work1.p, nX_, 2.0, Eslot);
+            DF_CHECK_LAUNCH();
+        }
         absmax_kernel<<<1, 1024, 0, s_>>>(Eslot, (long long)nX_ * nX_, d_scal_ + 3);
         DF_CHECK_LAUNCH();
         DF_CUDA(cudaMemcpyAsync(pin_, d_scal_, 4 * sizeof(double), cudaMemcpyDeviceToHost, s_));
@@ -477,6 +543,7 @@ class ScfRun {
             solve_orth();
             if (late_) diag_since_full_ = 0;
         }
+        first_factor_ = false;
         last_approx_ = approx;
     }
 
@@ -568,7 +635,31 @@ class ScfRun {
         eig(Fp_, nX_, h_->eps.p);
         vt_ = Fp_;
         fock_basis_ = true;
+        if (frac_) weight_occupied();
         occupy();
+    }
+
+    // fractional mode: occupations from the new orbital energies (read back: the atoms are small), the
+    // occupied eigenvectors weighted by sqrt(n_i / 2) into vto_
+    void weight_occupied() {
+        std::vector<double> eps(nX_);
+        DF_CUDA(cudaMemcpyAsync(eps.data(), h_->eps.p, sizeof(double) * nX_, cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaStreamSynchronize(s_));
+        const std::vector<double> occ = aufbau_occupations(eps, nelec_frac_);
+        occ_w_.assign(nX_, 0.0);
+        int m = 0;
+        for (int i = 0; i < nX_; ++i)
+            if (occ[i] > 0) {
+                occ_w_[i] = std::sqrt(occ[i] / 2.0);
+                m = i + 1;
+            }
+        if (m == 0) throw Error{DF_E_NUMERIC, "fractional occupation: no occupied orbital"};
+        nocc_ = m;
+        DF_CUDA(cudaMemcpyAsync(wocc_, occ_w_.data(), sizeof(double) * nX_, cudaMemcpyHostToDevice, s_));
+        weight_rows_kernel<<<nblk((long long)m * nX_), 256, 0, s_>>>(Fp_, wocc_, m, nX_, vto_);
+        DF_CHECK_LAUNCH();
+        DF_CUDA(cudaStreamSynchronize(s_));   // occ_w_ is read by the copy above
+        vt_ = vto_;
     }
 
     // approximate Roothaan step on the orthogonal-basis Fock matrix Fx: the rows of Fp_ (occupied first)
@@ -660,6 +751,8 @@ class ScfRun {
         if (Fo_) cudaFree(Fo_);
         if (abuf_) cudaFree(abuf_);
         abuf_ = nullptr;
+        if (vto_) cudaFree(vto_);
+        vto_ = wocc_ = nullptr;
         if (Kref_) cudaFree(Kref_);
         if (Cref_) cudaFree(Cref_);
         if (Wq_) cudaFree(Wq_);
@@ -707,12 +800,55 @@ class ScfRun {
     double e_old_ = 0.0, jk_ms_ = 0.0;
     bool done_ = false;
     int status_ = DF_E_NOTCONV;
+    bool frac_ = false;            // fractional occupations (set_fractional)
+    double nelec_frac_ = 0.0;
+    double* vto_ = nullptr;        // weighted occupied rows (fractional mode) | their weights (wocc_)
+    double* wocc_ = nullptr;
+    std::vector<double> occ_w_;
+    const double* C0_ = nullptr;   // initial factor (set_initial_factor): the first Fock matrix from 2 C0 C0^T
+    int m0_ = 0;
+    bool first_factor_ = false;    // the iteration being built uses C0 (no Roothaan step taken yet)
 };
 
 }  // namespace
 
+// Fractional-occupation SCF of one atom (handle ha, nelec electrons), FP64, converged to |dE| < 1e-11 and
+// max|e| < 1e-9: Cw (host, n x m row-major) receives the weighted occupied orbitals of the converged
+// density, D = 2 Cw Cw^T.
+void atomic_scf(df_handle* ha, double nelec, std::vector<double>& Cw, int& m) {
+    df_options o{};
+    o.conv_E = 1e-11;
+    o.conv_err = 1e-9;
+    o.max_iter = 200;
+    o.diis_size = 8;
+    o.guess = DF_GUESS_CORE;
+    o.precision = DF_PREC_FP64;
+    o.slices = 3;
+    df_result r{};
+    ScfRun run(ha, &o, &r);
+    run.set_fractional(nelec);
+    run.begin();
+    while (!run.done()) {
+        run.enqueue_iteration();
+        run.finish_iteration();
+    }
+    if (run.status() != DF_OK)
+        throw Error{DF_E_NUMERIC, "superposition-of-atomic-densities guess: the SCF of an atom (" +
+                                      std::to_string(nelec) + " electrons) did not converge"};
+    m = run.occupied_count();
+    Cw.resize((size_t)ha->n * m);
+    DF_CUDA(cudaStreamSynchronize(ha->stream));
+    DF_CUDA(cudaMemcpy(Cw.data(), run.occupied_factor(), sizeof(double) * Cw.size(), cudaMemcpyDeviceToHost));
+}
+
 int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess) {
     ScfRun run(h, o, r, guess);
+    DevBuf<double> C0;
+    if (!guess && o->guess == DF_GUESS_SAD) {
+        int m0 = 0;
+        sad_factor(h, C0, m0);
+        run.set_initial_factor(C0.p, m0);
+    }
     run.begin();
     while (!run.done()) {
         run.enqueue_iteration();
@@ -727,12 +863,19 @@ int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* gue
 // on its own stream) runs while the queued iterations of the others proceed on the GPU.
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs) {
     std::vector<std::unique_ptr<ScfRun>> runs;
+    std::vector<DevBuf<double>> factors(nmol);   // SAD starting factors, alive until the runs end
     for (int i = 0; i < nmol; ++i) {
         hs[i]->sync_timing = false;
         runs.emplace_back(new ScfRun(hs[i], o, &rs[i]));
     }
     int status = DF_OK;
     try {
+        if (o->guess == DF_GUESS_SAD)
+            for (int i = 0; i < nmol; ++i) {
+                int m0 = 0;
+                sad_factor(hs[i], factors[i], m0);
+                runs[i]->set_initial_factor(factors[i].p, m0);
+            }
         int started = 0, finished = 0;
         while (finished < nmol) {
             bool progressed = false;
