@@ -11,8 +11,10 @@
 // S <= 5), so the FP32 tensor-core sums are exact whatever the hardware's rounding. Pairs with s + t <= S + 1 are kept (the dropped pairs are
 // below 2^{-7(S+1)} relative). After each chunk the integer sums are scaled by the exact power of
 // two 2^{e_a + e_b - 7 L} and added into float-float accumulators (hi, lo) with Knuth's TwoSum.
-// Y leaves its kernel as (hi, lo) pairs, is re-split per (mu, block of P), and K leaves as (hi, lo)
-// partial sums that are combined in FP64.
+// Y leaves its kernel as (hi, lo) pairs and is re-split with one exponent per (mu, block of the contraction
+// over (P, i)): for the tensor-core contraction over the contiguous index k = P ldy + i in blocks of one
+// exact chunk, for the mma.sync contraction in blocks of whole auxiliary rows. K leaves as (hi, lo) partial
+// sums that are combined in FP64.
 // MMA: mma.sync m16n8k16 BF16 -> FP32 (warp-level), operands staged in shared memory by cp.async.
 #include <cuda_bf16.h>
 
@@ -393,6 +395,45 @@ __global__ void __launch_bounds__(256) split_y_kernel(const float2* __restrict__
         }
 }
 
+// Y (hi, lo) -> Ys[s][mu][k] over the contiguous contraction index k = P ldy + i (KL = naux ldy values per
+// row mu), one exponent per (mu, chunk of CH consecutive k): the operand layout of the tensor-core exchange
+// contraction (no padding between auxiliary rows); warp per (mu, chunk)
+template <int S>
+__global__ void __launch_bounds__(256) split_y_rows_kernel(const float2* __restrict__ Y, int np, int ldy, long long KL,
+                                                           int CH, bf16* __restrict__ Ys, int* __restrict__ Ye) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nchk = (KL + CH - 1) / CH;
+    if (warp >= nchk * np) return;
+    const int mu = (int)(warp % np);
+    const long long b = warp / np;
+    const long long k0 = b * CH, k1 = min(KL, k0 + CH);
+    auto at = [&](long long k) { return Y[((k / ldy) * np + mu) * ldy + k % ldy]; };
+    float mx = 0.f;
+    for (long long k = k0 + lane; k < k1; k += 32) mx = fmaxf(mx, fabsf(at(k).x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);   // |hi + lo| 2^-e <= 1 + 2^-24, so |m_1| <= 128 still holds
+    if (lane == 0) Ye[b * np + mu] = e;
+    const float sc = pow2f(-e);
+    const long long sstride = (long long)np * KL;
+    for (long long k = k0 + lane; k < k1; k += 32) {
+        const float2 y = at(k);
+        float r = y.x * sc;
+        float rl = y.y * sc;
+        bf16* out = Ys + (long long)mu * KL + k;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float tt = r * 128.f;
+            const float m = rintf(tt);
+            r = (tt - m) + rl * 128.f;
+            rl = 0.f;
+            out[s * sstride] = __float2bfloat16_rn(m);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // K partial sums over a range of auxiliary blocks for lower tile pair (I >= J) of 64 x 64
 // ------------------------------------------------------------------------------------------------
@@ -484,8 +525,8 @@ bool use_tensor_cores() {
 
 void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux,
                 int np, int ldy, float2* Y, int* err);
-void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB,
-                int nsplit, const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
+void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int nsplit,
+                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
 void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K);
 
 struct SplitState {
@@ -620,7 +661,7 @@ template <int S>
 void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
     cudaStream_t s = h->stream;
     const int np = st->np, ldy = st->ldy, naux = h->naux;
-    const long long nblk = (naux + st->PB - 1) / st->PB;
+    const long long nblk = ((long long)naux * ldy + exact_chunk<S>() - 1) / exact_chunk<S>();
     const int h0 = std::max(1, (int)std::min<long long>(st->ksplit_heur, nblk));   // occupancy heuristic
     if (h0 > st->kcap) {
         DF_CUDA(cudaStreamSynchronize(s));
@@ -633,8 +674,8 @@ void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
     double best_ms = 1e30;
     for (int N : {64, 32}) {
         const double ms = time_once(s, [&] {
-            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, st->PB, h0, st->tiles128, st->ntiles128,
-                       st->Kpart_tc, st->npt, st->err);
+            k_split_tc(s, S, N, st->Ys, st->Ye, naux, np, ldy, h0, st->tiles128, st->ntiles128, st->Kpart_tc,
+                       st->npt, st->err);
         });
         if (ms < best_ms) {
             best_ms = ms;
@@ -714,9 +755,17 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         const int nyb = (naux + pblk - 1) / pblk;   // split C, per block (slicing,) Y, re-split Y, K, reduce
         h->exchange_launches = 4 + nyb * (st->blocked ? 2 : 1);
     }
-    const long long nblk = (naux + st->PB - 1) / st->PB;
     const long long ystr = (long long)naux * np * ldy;
-    split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr, st->Ye);
+    // the tensor-core contraction takes Ys[s][mu][k] (k = P ldy + i, chunks of the exact length for S); the
+    // mma.sync contraction Ys[s][P][mu][i] with chunks of PB auxiliary rows
+    const long long nblk = tc ? ((long long)naux * ldy + exact_chunk<S>() - 1) / exact_chunk<S>()
+                              : (naux + st->PB - 1) / st->PB;
+    if (tc)
+        split_y_rows_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, np, ldy, (long long)naux * ldy,
+                                                                           exact_chunk<S>(), st->Ys, st->Ye);
+    else
+        split_y_kernel<S><<<nblocks(nblk * np * 32, 256), 256, 0, s>>>(st->Y, naux, np, ldy, st->PB, st->Ys, ystr,
+                                                                      st->Ye);
     DF_CHECK_LAUNCH();
     if (tc) {
         if (!have) {
@@ -727,7 +776,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
             g_tune.emplace(key, ch);   // the first tuned choice of a bucket stays
             g_tune_ms += tune_ms;
         }
-        // a choice made for another handle of the bucket: at most one split per auxiliary block, and room
+        // a choice made for another handle of the bucket: at most one split per exponent block, and room
         // for it in the partial-sum buffer
         // the override's split, else this state's own heuristic (a cached choice carries only widths)
         const int ksplit = (int)std::min<long long>(std::getenv("DFHF_TC_TILES") && ch.ksplit > 0 ? ch.ksplit
@@ -754,8 +803,8 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         }
         h->timings_ms[15] = ch.kN;
         DF_CUDA(cudaEventRecord(ev[2], s));
-        k_split_tc(s, S, ch.kN, st->Ys, st->Ye, naux, np, ldy, st->PB, ksplit, st->tiles128, st->ntiles128,
-                   st->Kpart_tc, st->npt, st->err);
+        k_split_tc(s, S, ch.kN, st->Ys, st->Ye, naux, np, ldy, ksplit, st->tiles128, st->ntiles128, st->Kpart_tc,
+                   st->npt, st->err);
         DF_CUDA(cudaEventRecord(ev[3], s));
         k_tc_reduce(s, st->Kpart_tc, ksplit, st->npt, h->n, dK);
     } else {
@@ -848,8 +897,11 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
         DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
         DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * (long long)h->naux * np * ldy));
+        // exponents per block: PB auxiliary rows (mma.sync layout) or an exact chunk of the contiguous
+        // contraction index (tensor-core layout; the shortest chunk, S = SMAX, has the most blocks)
         const long long nblk = (h->naux + st->PB - 1) / st->PB;
-        DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * nblk * np));
+        const long long nchk = ((long long)h->naux * ldy + exact_chunk<SMAX>() - 1) / exact_chunk<SMAX>();
+        DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * std::max(nblk, nchk) * np));
         DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
         // tcgen05 K: lower 128-tile pairs, split over auxiliary blocks to fill the GPU
         if (!st->err) {
@@ -866,7 +918,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         st->tiles128 = nullptr;
         DF_CUDA(cudaMalloc((void**)&st->tiles128, sizeof(int2) * t128.size()));
         DF_CUDA(cudaMemcpy(st->tiles128, t128.data(), sizeof(int2) * t128.size(), cudaMemcpyHostToDevice));
-        st->nsplit_tc = std::max(1, std::min((4 * 152 + 2 * st->ntiles128 - 1) / (2 * st->ntiles128), (int)nblk));
+        st->nsplit_tc = std::max(1, std::min((4 * 152 + 2 * st->ntiles128 - 1) / (2 * st->ntiles128), (int)nchk));
         st->ksplit_heur = st->nsplit_tc;
         cudaFree(st->Kpart_tc);
         st->Kpart_tc = nullptr;

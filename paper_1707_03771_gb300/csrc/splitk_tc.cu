@@ -149,14 +149,18 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 // ------------------------------------------------------------------------------------------------
 // Work description. MODE 0 (Y = B C): CTA = (P, mu-tile, n-tile); K runs over nu (np), exponents
-// constant (row: Be[P][mu], column: Ce[i]). MODE 1 (K = sum Y Y^T): CTA = (lower tile pair, half,
-// split); K runs over auxiliary rows P in [p0, p1) and, inside each, over i (ldy, 64-steps), with one
-// chunk per block of PB rows (exponents Ye[block][mu], Ye[block][nu]).
+// constant (row: Be[P][mu], column: Ce[i]). MODE 1 (K = sum Y Y^T): CTA = (split, lower tile pair,
+// column part), the split slowest so that the CTAs resident together stream the same range of the
+// contraction through L2; K runs over the contiguous index k = P ldy + i of the Y slices Ys[s][mu][k]
+// (no padding between auxiliary rows), one exact chunk per block of `chunk` consecutive k with its own
+// exponents Ye[block][mu], Ye[block][nu].
 // ------------------------------------------------------------------------------------------------
 struct TcArgs {
     int mode;
     int naux, np, ldy, PB, nsplit;
-    const int* row_e;        // MODE 0: Be [naux][np]; MODE 1: Ye [nblk][np]
+    long long KL;            // MODE 1: naux * ldy, the length of the contraction
+    int ntiles;              // MODE 1: lower 128-tile pairs
+    const int* row_e;        // MODE 0: Be [naux][np]; MODE 1: Ye [nchunk][np]
     const int* col_e;        // MODE 0: Ce [ldy]
     const int2* tiles;       // MODE 1: lower 128-tile pairs
     float2* out;             // MODE 0: Y [naux][np][ldy]; MODE 1: Kpart [nsplit][npt][npt]
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     int P = 0, m0 = 0, n0 = 0, split = 0;
     int2 IJ = make_int2(0, 0);
     int ksteps = 0;
-    int p0 = 0, p1 = 0, kpp = 0;
+    int p0 = 0, kpp = 0;   // MODE 1: first chunk and first K-step of the split
     if (MODE == 0) {
         const int mt = (args.np + TM - 1) / TM;
         const int nt = args.ldy / N;
@@ -223,16 +227,17 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         int b = blockIdx.x;
         const int h = b % halves;
         b /= halves;
-        split = b % args.nsplit;
-        IJ = args.tiles[b / args.nsplit];
+        IJ = args.tiles[b % args.ntiles];
+        split = b / args.ntiles;
         m0 = IJ.x * TM;
         n0 = IJ.y * TM + h * N;
-        const int nblk = (args.naux + args.PB - 1) / args.PB;
-        const int b0 = (int)((long long)nblk * split / args.nsplit), b1 = (int)((long long)nblk * (split + 1) / args.nsplit);
-        p0 = b0 * args.PB;
-        p1 = min(args.naux, b1 * args.PB);
-        kpp = (args.ldy + KS - 1) / KS;
-        ksteps = (p1 - p0) * kpp;
+        constexpr int CH = exact_chunk<S>();
+        const long long nchk = (args.KL + CH - 1) / CH;
+        const long long c0 = nchk * split / args.nsplit, c1 = nchk * (split + 1) / args.nsplit;
+        p0 = (int)c0;                                              // first chunk of this split
+        const long long k0 = c0 * CH, k1 = min(args.KL, c1 * CH);
+        kpp = (int)(k0 / KS);                                      // first K-step (chunks are K-step aligned)
+        ksteps = (int)((k1 - k0 + KS - 1) / KS);
     }
 
     // ---- set-up: barriers (thread 0), tensor memory (warp 0) ------------------------------------
@@ -260,10 +265,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     fence_after();
     const unsigned tmem = *tmem_slot;
 
-    // chunk index of K-step ks (MODE 0 and 2: the exact chunk of S slices; MODE 1: PB auxiliary rows)
-    auto chunk_of = [&](int ks) {
-        return MODE == 1 ? (ks / kpp) / args.PB : ks / chunk_steps<S>();
-    };
+    // chunk index of K-step ks (every mode: the exact chunk of S slices)
+    auto chunk_of = [&](int ks) { return ks / chunk_steps<S>(); };
     const int nchunks = ksteps > 0 ? chunk_of(ksteps - 1) + 1 : 0;
 
     if (warp == 4) {
@@ -273,16 +276,12 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
             asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapB) : "memory");
             int a_issued = 0, b_issued = 0;
             for (int ks = 0; ks < ksteps; ++ks) {
-                // tensor coordinates of this K-step: x (contraction), the auxiliary row for MODE 1
-                const int kx = MODE == 1 ? (ks % kpp) * KS : ks * KS;
-                const int Pr = MODE == 1 ? p0 + ks / kpp : 0;
+                // x: the contraction coordinate of this K-step (MODE 1: from the split's first K-step)
+                const int kx = MODE == 1 ? (kpp + ks) * KS : ks * KS;
                 const int bs = ks & 1;
                 if (!mbar_wait(&b_empty[bs], ((ks >> 1) & 1) ^ 1, err, wait)) break;
                 mbar_expect_tx(&b_full[bs], BSET);
-                for (int t = 0; t < S; ++t) {
-                    const int zb = MODE == 1 ? t * args.naux + Pr : t;
-                    tma_load_3d(bbuf + bs * BSET + t * B_BYTES, &mapB, kx, n0, zb, &b_full[bs]);
-                }
+                for (int t = 0; t < S; ++t) tma_load_3d(bbuf + bs * BSET + t * B_BYTES, &mapB, kx, n0, t, &b_full[bs]);
                 ++b_issued;
                 bool ok = true;
                 for (int s = 0; s < S; ++s) {
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                         break;
                     }
                     mbar_expect_tx(&a_full[slot], A_BYTES);
-                    const int za = MODE == 0 ? s * args.naux + P : (MODE == 2 ? s : s * args.naux + Pr);
+                    const int za = MODE == 0 ? s * args.naux + P : s;
                     tma_load_3d(smem + slot * A_BYTES, &mapA, kx, m0, za, &a_full[slot]);
                     ++a_issued;
                 }
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
             int erow = 0;
             long long blk = 0;
             if (MODE == 1) {
-                blk = p0 / args.PB + ch;
+                blk = p0 + ch;
                 erow = (grow < args.np) ? args.row_e[blk * args.np + grow] : 0;
             }
             if (!mbar_wait(acc_full, ch & 1, err, wait)) break;
@@ -588,24 +587,26 @@ void whiten_tc(cudaStream_t s, int N, const bf16* Ls, const int* eL, const bf16*
     else throw Error{DF_E_ARG, "tensor-core whitening supports tile widths 32 and 64"};
 }
 
-// K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs)
+// K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs), from the Y slices
+// Ys [S][np][KL] (KL = naux ldy, contraction index k = P ldy + i contiguous) with exponents Ye [chunk][np]
 template <int N>
-void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB, int nsplit,
+void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int nsplit,
                   const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
     TcArgs a{};
     a.mode = 1;
     a.naux = naux;
     a.np = np;
     a.ldy = ldy;
-    a.PB = PB;
+    a.KL = (long long)naux * ldy;
+    a.ntiles = ntiles;
     a.nsplit = nsplit;
     a.row_e = Ye;
     a.tiles = tiles128;
     a.out = Kpart;
     a.npt = npt;
     a.err = err;
-    const CUtensorMap ma = make_map(Ys, ldy, np, (unsigned long long)S * naux, TM);
-    const CUtensorMap mb = make_map(Ys, ldy, np, (unsigned long long)S * naux, N);
+    const CUtensorMap ma = make_map(Ys, (unsigned long long)a.KL, np, S, TM);
+    const CUtensorMap mb = make_map(Ys, (unsigned long long)a.KL, np, S, N);
     const unsigned grid = (unsigned)ntiles * nsplit * (TM / N);
     switch (S) {
         case 3: launch_tc<3, N, 1>(s, ma, mb, a, grid); break;
@@ -615,10 +616,10 @@ void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux
 }
 
 // N: width of the column half-tiles of each 128 x 128 output tile, 64 or 32
-void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int PB,
-                int nsplit, const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
-    if (N == 64) k_split_tc_n<64>(s, S, Ys, Ye, naux, np, ldy, PB, nsplit, tiles128, ntiles, Kpart, npt, err);
-    else if (N == 32) k_split_tc_n<32>(s, S, Ys, Ye, naux, np, ldy, PB, nsplit, tiles128, ntiles, Kpart, npt, err);
+void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int nsplit,
+                const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
+    if (N == 64) k_split_tc_n<64>(s, S, Ys, Ye, naux, np, ldy, nsplit, tiles128, ntiles, Kpart, npt, err);
+    else if (N == 32) k_split_tc_n<32>(s, S, Ys, Ye, naux, np, ldy, nsplit, tiles128, ntiles, Kpart, npt, err);
     else throw Error{DF_E_ARG, "tensor-core split K supports tile widths 32 and 64"};
 }
 

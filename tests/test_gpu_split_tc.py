@@ -1,6 +1,8 @@
 """The tcgen05 (TMEM + TMA) split-precision kernels against the mma.sync split kernels and the FP64
-path on the same B and C. Both split paths form the same exact integer chunk sums, so they agree to
-the FP64 rounding of their final sums."""
+path on the same B and C. The two paths slice B and C identically and form the same exact Y; they
+re-slice Y with exponents over different blocks of the (P, i) contraction (the tensor-core contraction
+over chunks of the contiguous index P ldy + i, the mma.sync one over whole auxiliary rows), so their K
+differ by the splitting error: each is held to the bound 2^(7 - 7S) against FP64, and the two to twice it."""
 import os
 
 import numpy as np
@@ -44,9 +46,13 @@ def test_tensor_core_split_matches_mma_sync_and_fp64(lib, name, slices):
         Ktc = _k(h, lib, D, C, slices, tc=True)
         Ktc2 = _k(h, lib, D, C, slices, tc=True)
     scale = np.abs(K64).max()
+    bound = 2.0 ** (7 - 7 * slices)
+    print(f"{name} S={slices}: tcgen05 {np.abs(Ktc - K64).max() / scale:.2e}, mma.sync "
+          f"{np.abs(Kms - K64).max() / scale:.2e} relative to FP64")
     assert np.array_equal(Ktc, Ktc2)
-    assert np.abs(Ktc - Kms).max() <= 1e-12 * scale, np.abs(Ktc - Kms).max() / scale
-    assert np.abs(Ktc - K64).max() <= 2.0 ** (7 - 7 * slices) * scale
+    assert np.abs(Ktc - K64).max() <= bound * scale
+    assert np.abs(Kms - K64).max() <= bound * scale
+    assert np.abs(Ktc - Kms).max() <= 2 * bound * scale
 
 
 def test_autotuner_choice_is_valid_and_cached(lib):
