@@ -549,6 +549,9 @@ struct SplitState {
     int* Ye = nullptr;
     float2* Kpart = nullptr;
     int ldy = 0;
+    int ldy_cap = 0;             // occupied width the Cs, Ce, Y and Ys buffers were sized for
+    long long ye_cap = 0;        // entries of Ye
+    int kpart_cap = 0;           // splits Kpart has room for (mma.sync contraction)
     int nsplit = 0;
     int PB = 0;
     bool blocked = false;        // B slices cut per block of pblk auxiliary rows at every build
@@ -880,50 +883,71 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     }
     if (ldy != st->ldy) {
         DF_CUDA(cudaStreamSynchronize(h->stream));   // earlier builds may still read these buffers
-        cudaFree(st->Cs);
-        cudaFree(st->Ce);
-        cudaFree(st->Y);
-        cudaFree(st->Ys);
-        cudaFree(st->Ye);
-        cudaFree(st->Kpart);
-        st->ldy = ldy;
-        st->PB = std::max(1, (CHUNK_TILES * KT) / ldy);
         if (ldy > CHUNK_TILES * KT) throw Error{DF_E_ARG, "split exchange supports nocc <= 512"};
+        st->ldy = ldy;
+        // the tile choices were made for the previous occupied width (a width need not divide the new one)
+        for (int q = 0; q <= SMAX; ++q) st->ch_y[q] = st->ch_k[q] = st->ch_split[q] = 0;
+        st->PB = std::max(1, (CHUNK_TILES * KT) / ldy);
         const int nt = st->np / 64;
         const int ntiles = nt * (nt + 1) / 2;
         st->nsplit = std::max(1, std::min((8 * 152 + ntiles - 1) / ntiles, (h->naux + st->PB - 1) / st->PB));
         const long long np = st->np;
-        DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * st->S * (long long)ldy * np));
-        DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
-        DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
-        DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * (long long)h->naux * np * ldy));
+        // buffers keep the largest width met (an SCF from the SAD factor builds its first exchange wider):
+        // a narrower build reuses them without reallocating
+        if (ldy > st->ldy_cap) {
+            cudaFree(st->Cs);
+            cudaFree(st->Ce);
+            cudaFree(st->Y);
+            cudaFree(st->Ys);
+            st->Cs = nullptr;
+            st->Ce = nullptr;
+            st->Y = nullptr;
+            st->Ys = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * st->S * (long long)ldy * np));
+            DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
+            DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
+            DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * (long long)h->naux * np * ldy));
+            st->ldy_cap = ldy;
+        }
         // exponents per block: PB auxiliary rows (mma.sync layout) or an exact chunk of the contiguous
         // contraction index (tensor-core layout; the shortest chunk, S = SMAX, has the most blocks)
         const long long nblk = (h->naux + st->PB - 1) / st->PB;
         const long long nchk = ((long long)h->naux * ldy + exact_chunk<SMAX>() - 1) / exact_chunk<SMAX>();
-        DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * std::max(nblk, nchk) * np));
-        DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
-        // tcgen05 K: lower 128-tile pairs, split over auxiliary blocks to fill the GPU
+        if (std::max(nblk, nchk) * np > st->ye_cap) {
+            cudaFree(st->Ye);
+            st->Ye = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Ye, sizeof(int) * std::max(nblk, nchk) * np));
+            st->ye_cap = std::max(nblk, nchk) * np;
+        }
+        if (st->nsplit > st->kpart_cap) {
+            cudaFree(st->Kpart);
+            st->Kpart = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Kpart, sizeof(float2) * st->nsplit * np * np));
+            st->kpart_cap = st->nsplit;
+        }
         if (!st->err) {
             DF_CUDA(cudaMalloc((void**)&st->err, sizeof(int)));
             DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
         }
-        const int nt128 = (int)((np + 127) / 128);
-        st->npt = nt128 * 128;
-        st->ntiles128 = nt128 * (nt128 + 1) / 2;
-        std::vector<int2> t128;
-        for (int I = 0; I < nt128; ++I)
-            for (int J = 0; J <= I; ++J) t128.push_back(make_int2(I, J));
-        cudaFree(st->tiles128);
-        st->tiles128 = nullptr;
-        DF_CUDA(cudaMalloc((void**)&st->tiles128, sizeof(int2) * t128.size()));
-        DF_CUDA(cudaMemcpy(st->tiles128, t128.data(), sizeof(int2) * t128.size(), cudaMemcpyHostToDevice));
+        // tcgen05 K: lower 128-tile pairs (fixed by np), split over exponent blocks to fill the GPU
+        if (!st->tiles128) {
+            const int nt128 = (int)((np + 127) / 128);
+            st->npt = nt128 * 128;
+            st->ntiles128 = nt128 * (nt128 + 1) / 2;
+            std::vector<int2> t128;
+            for (int I = 0; I < nt128; ++I)
+                for (int J = 0; J <= I; ++J) t128.push_back(make_int2(I, J));
+            DF_CUDA(cudaMalloc((void**)&st->tiles128, sizeof(int2) * t128.size()));
+            DF_CUDA(cudaMemcpy(st->tiles128, t128.data(), sizeof(int2) * t128.size(), cudaMemcpyHostToDevice));
+        }
         st->nsplit_tc = std::max(1, std::min((4 * 152 + 2 * st->ntiles128 - 1) / (2 * st->ntiles128), (int)nchk));
         st->ksplit_heur = st->nsplit_tc;
-        cudaFree(st->Kpart_tc);
-        st->Kpart_tc = nullptr;
-        DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * st->nsplit_tc * (long long)st->npt * st->npt));
-        st->kcap = st->nsplit_tc;
+        if (st->nsplit_tc > st->kcap) {
+            cudaFree(st->Kpart_tc);
+            st->Kpart_tc = nullptr;
+            DF_CUDA(cudaMalloc((void**)&st->Kpart_tc, sizeof(float2) * st->nsplit_tc * (long long)st->npt * st->npt));
+            st->kcap = st->nsplit_tc;
+        }
     }
     // synchronous callers clear the timeout flag per call; under the SCF driver it stays set once
     // raised and is read with the iteration's scalars
