@@ -143,6 +143,14 @@ int df_build_B(df_handle* h, double screen_tau, int keep_3c);
  * drops the split-precision slices cut from the previous B. */
 int df_build_B_ex(df_handle* h, double screen_tau, int keep_3c, int whitening);
 
+/* B for n molecules (distinct handles on one device; the batched form of df_build_B_ex, the paper has no
+ * counterpart): the three-centre integrals of all of them run as one persistent launch per angular-momentum
+ * class over a global queue of (molecule, block of 128 shell pairs, block of 8 auxiliary shells) work items,
+ * then each molecule's metric factor, inverse and whitening follow on its own stream. The integrals are
+ * bitwise those of df_build_B. Every handle needs room for its integrals at once. Returns the first failure
+ * (each handle's df_last_error holds it); handles left without B are reset. */
+int df_build_B_batch(df_handle** hs, int n, double screen_tau, int keep_3c, int whitening);
+
 /* Coulomb and exchange matrices (paper eq. 3, first two forms, and eqs. 1-2, first forms) for density
  * D (n x n, symmetric) and occupied coefficients C_occ (n x nocc, row-major: C_occ[mu * nocc + i]):
  *   J = sum_P gamma_P B_P with gamma_P = sum B_{P,mu nu} D_{mu nu};  K = sum_{P,i} Y Y^T.
@@ -158,7 +166,9 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
  * Results in *out; returns out->status. */
 int scf_run(df_handle* h, const df_options* opts, df_result* out);
 
-/* Batched SCF: nmol independent molecules (distinct handles on one device) solved together. Each
+/* Batched SCF: nmol independent molecules (distinct handles on one device) solved together. Handles
+ * without B get their three-centre integrals from one grouped launch per class (as df_build_B_batch) before
+ * the iterations start; each molecule's metric factor and whitening run when it starts. Each
  * molecule's iteration is enqueued on its own stream; one host thread polls the molecules' completion
  * events and advances whichever has finished (convergence test, DIIS, orbital step, next iteration),
  * starting one more molecule per pass, so kernels of different molecules overlap on the GPU. B is built

@@ -22,7 +22,7 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
-            "df_fp64_rate", "df_sad_density"]
+            "df_fp64_rate", "df_sad_density", "df_build_B_batch"]
 DF_MLP_NFEAT = 57
 
 
@@ -85,6 +85,7 @@ def load(path: str | None = None):
     L.df_prepare.argtypes = []
     L.df_fp64_rate.argtypes = [c_int, ctypes.c_longlong, dp, dp]
     L.df_sad_density.argtypes = [c_void_p, dp]
+    L.df_build_B_batch.argtypes = [P(c_void_p), c_int, c_double, c_int, c_int]
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
@@ -308,6 +309,16 @@ def scf_batch(handles, conv_E=1e-10, conv_err=1e-7, max_iter=100, diis_size=8, p
         detail = "; ".join(f"molecule {i}: status {st}: {msg}" for i, st, msg in failed[:4])
         raise DFError(rc, f"scf_run_batch: {len(failed)} of {n} failed: {detail}")
     return [out[i].as_dict() for i in range(n)]
+
+
+def build_B_batch(handles, screen_tau=0.0, keep_3c=False, whitening=DF_WHITEN_SPLIT):
+    """B for several molecules (df_build_B_batch): grouped three-centre integrals, then each molecule's
+    metric factor and whitening."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[hd.h.value for hd in handles])
+    rc = load().df_build_B_batch(hs, n, screen_tau, int(keep_3c), int(whitening))
+    if rc != DF_OK:
+        raise DFError(rc, "df_build_B_batch: " + load().df_last_error(handles[0].h).decode())
 
 
 def _fp(a):

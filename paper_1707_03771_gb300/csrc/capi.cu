@@ -197,10 +197,14 @@ void build_B(df_handle* h, double tau, bool keep, int whitening) {
     cudaEvent_t ev[4];
     for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
     h->B.release();
-    h->A3c.release();
-    h->A3c.alloc(rows);
+    const bool have_3c = h->a3c_ready && h->A3c.p && h->A3c.n == rows;
+    h->a3c_ready = false;
+    if (!have_3c) {
+        h->A3c.release();
+        h->A3c.alloc(rows);
+    }
     DF_CUDA(cudaEventRecord(ev[0], s));
-    compute_three_center(h, h->A3c.p, tau);
+    if (!have_3c) compute_three_center(h, h->A3c.p, tau);
     DF_CUDA(cudaEventRecord(ev[1], s));
     // metric Cholesky (P|Q) = L L^T: cuSOLVER works column-major, so the upper factor U (V = U^T U)
     // of the column-major matrix is the row-major lower factor L = U^T (trtri of U would give L^-1).
@@ -301,6 +305,30 @@ void build_B(df_handle* h, double tau, bool keep, int whitening) {
     if (!keep) h->A3c.release();
     h->built = true;
     h->whitening = whitening;
+}
+
+// B for several handles: the three-centre integrals of all of them in one grouped launch per class (on
+// the first handle's stream), then, if whiten_now, each handle's metric factor, inverse and whitening;
+// otherwise the handles keep their integrals (a3c_ready) for build_B to finish later
+void build_B_batch(df_handle** hs, int n, double tau, bool keep, int whitening, bool whiten_now) {
+    std::vector<df_handle*> need;
+    std::vector<double*> outs;
+    for (int i = 0; i < n; ++i) {
+        df_handle* h = hs[i];
+        if (h->built) continue;
+        h->B.release();
+        h->A3c.release();
+        h->A3c.alloc((size_t)h->naux * h->pk.row);
+        h->a3c_ready = false;
+        need.push_back(h);
+        outs.push_back(h->A3c.p);
+    }
+    if (need.empty()) return;
+    for (df_handle* h : need) DF_CUDA(cudaStreamSynchronize(h->stream));   // nothing queued reads A3c
+    compute_three_center_grouped(need, outs, need[0]->stream);           // returns with the work done
+    for (df_handle* h : need) h->a3c_ready = true;
+    if (whiten_now)
+        for (df_handle* h : need) build_B(h, tau, keep, whitening);
 }
 
 void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
@@ -488,6 +516,35 @@ int df_build_B_ex(df_handle* h, double screen_tau, int keep_3c, int whitening) {
         h->A3c.release();
         h->built = false;
         return fail(h, e);
+    }
+    return DF_OK;
+}
+
+int df_build_B_batch(df_handle** hs, int n, double screen_tau, int keep_3c, int whitening) {
+    if (!hs || n < 1 || screen_tau < 0 || (whitening != DF_WHITEN_SPLIT && whitening != DF_WHITEN_FP64)) return DF_E_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return DF_E_ARG;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return DF_E_ARG;
+        if (hs[i]->device != hs[0]->device) return DF_E_ARG;
+    }
+    try {
+        DF_CUDA(cudaSetDevice(hs[0]->device));
+        for (int i = 0; i < n; ++i) {
+            free_split(hs[i]);
+            hs[i]->built = false;
+        }
+        build_B_batch(hs, n, screen_tau, keep_3c != 0, whitening, true);
+    } catch (const Error& e) {
+        for (int i = 0; i < n; ++i) {
+            hs[i]->last_error = e.msg;
+            if (!hs[i]->built) {
+                hs[i]->B.release();
+                hs[i]->A3c.release();
+                hs[i]->a3c_ready = false;
+            }
+        }
+        return e.code;
     }
     return DF_OK;
 }

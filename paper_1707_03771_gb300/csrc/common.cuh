@@ -150,6 +150,7 @@ struct df_handle {
     dfhf::DevBuf<double> A3c, B;
     bool built = false;
     int whitening = DF_WHITEN_SPLIT;   // how B was whitened (DF_WHITEN_*)
+    bool a3c_ready = false;            // A3c already holds (P|mu nu) (grouped integrals of a batch)
 
     // J/K work
     dfhf::DevBuf<double> Dw, gamma, Jp, Y, Kpart, Cpad, dD, dC, dJ, dK;
@@ -182,6 +183,10 @@ int init_handle(const df_atom* atoms, int natom, const df_shell* basis, int nbas
 void compute_one_electron(df_handle* h);
 void compute_metric(df_handle* h);
 void compute_three_center(df_handle* h, double* out, double tau);
+void compute_three_center_grouped(const std::vector<df_handle*>& hs, const std::vector<double*>& outs,
+                                  cudaStream_t s);
+void build_B(df_handle* h, double tau, bool keep, int whitening);
+void build_B_batch(df_handle** hs, int n, double tau, bool keep, int whitening, bool whiten_now);
 void rys_eval(const double* dT, int count, int n, double* dx, double* dw, cudaStream_t s);
 
 // FP64 dense kernels (dense.cu)

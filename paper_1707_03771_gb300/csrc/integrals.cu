@@ -4,7 +4,9 @@
 // Paper, section "Molecular integrals": the 1/r12 integrals are computed by Rys quadrature over shell
 // objects, and the nuclear attraction needs the molecule as well. One kernel is instantiated per
 // angular-momentum class; one thread evaluates one shell triple (or shell pair) with rys_eri.cuh.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "rys_eri.cuh"
@@ -75,9 +77,44 @@ __device__ __forceinline__ void load3(const double* __restrict__ xyz, int s, dou
 }
 
 // ---------------------------------------------------------------------------------------------
-// three-centre (P|ab): threads over orbital shell pairs of one class, blockIdx.y over auxiliary
-// shells of angular momentum LP; output rows of `row` doubles, packed mu >= nu tiles
+// three-centre (P|ab) of one shell triple: pair (a, b) of class (LA, LB), auxiliary shell P of
+// angular momentum LP; written into rows of `row` doubles, packed mu >= nu tiles
 // ---------------------------------------------------------------------------------------------
+template <int LP, int LA, int LB>
+__device__ __forceinline__ void eri3c_triple(const ShellView& bas, const ShellView& aux, int a, int b, const double* A,
+                                             const double* B, int P, const double* __restrict__ tab,
+                                             double* __restrict__ out, long long row) {
+    const double aa = bas.alpha[a], ab = bas.alpha[b];
+    const double nab = bas.norm[a] * bas.norm[b];
+    const int offa = bas.off[a], offb = bas.off[b];
+    double C[3];
+    load3(aux.xyz, P, C);
+    RysParams q;
+    constexpr int N = NR<LP + LA + LB>::value;
+    double x[N], w[N];
+    setup_3c<N>(aa, A, ab, B, aux.alpha[P], C, tab, q, x, w);
+    double cart[ncart(LP) * ncart(LA) * ncart(LB)];
+    rys_cart<LP, LA, LB>(q, x, w, cart);
+    double sph[nsph(LP) * nsph(LA) * nsph(LB)];
+    cart_to_sph<LP, LA, LB>(cart, sph);
+    const double scale = nab * aux.norm[P];
+    const int offp = aux.off[P];
+#pragma unroll
+    for (int mp = 0; mp < nsph(LP); ++mp) {
+        double* o = out + (long long)(offp + mp) * row;
+#pragma unroll
+        for (int ma = 0; ma < nsph(LA); ++ma)
+#pragma unroll
+            for (int mb = 0; mb < nsph(LB); ++mb) {
+                const int mu = offa + ma, nu = offb + mb;
+                const double v = scale * sph[(mp * nsph(LA) + ma) * nsph(LB) + mb];
+                o[packed_index(mu, nu)] = v;
+                if (mu / TS == nu / TS) o[packed_index(nu, mu)] = v;
+            }
+    }
+}
+
+// threads over orbital shell pairs of one class, blockIdx.y over auxiliary shells of angular momentum LP
 template <int LP, int LA, int LB>
 __global__ void __launch_bounds__(128) eri3c_kernel(ShellView bas, ShellView aux, const int2* __restrict__ pairs,
                                                     int npairs, const int* __restrict__ auxl, int naux_l,
@@ -86,39 +123,63 @@ __global__ void __launch_bounds__(128) eri3c_kernel(ShellView bas, ShellView aux
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npairs) return;
     const int2 pr = pairs[ip];
-    const int a = pr.x, b = pr.y;
     double A[3], B[3];
-    load3(bas.xyz, a, A);
-    load3(bas.xyz, b, B);
-    const double aa = bas.alpha[a], ab = bas.alpha[b];
-    const double nab = bas.norm[a] * bas.norm[b];
-    const int offa = bas.off[a], offb = bas.off[b];
-    for (int ia = blockIdx.y; ia < naux_l; ia += gridDim.y) {
-        const int P = auxl[ia];
-        double C[3];
-        load3(aux.xyz, P, C);
-        RysParams q;
-        constexpr int N = NR<LP + LA + LB>::value;
-        double x[N], w[N];
-        setup_3c<N>(aa, A, ab, B, aux.alpha[P], C, tab, q, x, w);
-        double cart[ncart(LP) * ncart(LA) * ncart(LB)];
-        rys_cart<LP, LA, LB>(q, x, w, cart);
-        double sph[nsph(LP) * nsph(LA) * nsph(LB)];
-        cart_to_sph<LP, LA, LB>(cart, sph);
-        const double scale = nab * aux.norm[P];
-        const int offp = aux.off[P];
-#pragma unroll
-        for (int mp = 0; mp < nsph(LP); ++mp) {
-            double* o = out + (long long)(offp + mp) * row;
-#pragma unroll
-            for (int ma = 0; ma < nsph(LA); ++ma)
-#pragma unroll
-                for (int mb = 0; mb < nsph(LB); ++mb) {
-                    const int mu = offa + ma, nu = offb + mb;
-                    const double v = scale * sph[(mp * nsph(LA) + ma) * nsph(LB) + mb];
-                    o[packed_index(mu, nu)] = v;
-                    if (mu / TS == nu / TS) o[packed_index(nu, mu)] = v;
-                }
+    load3(bas.xyz, pr.x, A);
+    load3(bas.xyz, pr.y, B);
+    for (int ia = blockIdx.y; ia < naux_l; ia += gridDim.y)
+        eri3c_triple<LP, LA, LB>(bas, aux, pr.x, pr.y, A, B, auxl[ia], tab, out, row);
+}
+
+// ---------------------------------------------------------------------------------------------
+// three-centre integrals of many molecules in one persistent launch per class: a global queue of work
+// items (molecule, block of 128 shell pairs, block of AUX_PER_ITEM auxiliary shells), taken in order by
+// resident CTAs through an atomic counter; the molecule of an item is found by binary search over the
+// prefix sums of the molecules' item counts.
+// ---------------------------------------------------------------------------------------------
+constexpr int AUX_PER_ITEM = 8;
+
+struct Mol3c {
+    ShellView bas, aux;
+    const int2* pairs;       // the class's pair list
+    int npairs;
+    const int* auxl;         // auxiliary shells of angular momentum LP
+    int naux_l;
+    double* out;
+    long long row;
+};
+
+template <int LP, int LA, int LB>
+__global__ void __launch_bounds__(128) eri3c_grouped_kernel(const Mol3c* __restrict__ mols,
+                                                            const long long* __restrict__ item_off, int nmol,
+                                                            unsigned long long* __restrict__ counter,
+                                                            const double* __restrict__ tab) {
+    __shared__ long long s_item;
+    const long long total = item_off[nmol];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= total) return;
+        int lo = 0, hi = nmol;   // the molecule m with item_off[m] <= item < item_off[m + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const Mol3c& M = mols[lo];
+        const long long local = item - item_off[lo];
+        const int npb = (M.npairs + 127) / 128;
+        const int pb = (int)(local % npb), ab = (int)(local / npb);
+        const int ip = pb * 128 + threadIdx.x;
+        if (ip < M.npairs) {
+            const int2 pr = M.pairs[ip];
+            double A[3], B[3];
+            load3(M.bas.xyz, pr.x, A);
+            load3(M.bas.xyz, pr.y, B);
+            const int a1 = min(M.naux_l, (ab + 1) * AUX_PER_ITEM);
+            for (int ia = ab * AUX_PER_ITEM; ia < a1; ++ia)
+                eri3c_triple<LP, LA, LB>(M.bas, M.aux, pr.x, pr.y, A, B, M.auxl[ia], tab, M.out, M.row);
         }
     }
 }
@@ -372,6 +433,69 @@ void compute_three_center(df_handle* h, double* out, double tau) {
             DF_CHECK_LAUNCH();
         }
     }
+}
+
+// Three-centre integrals of several molecules (outs[i]: rows of hs[i]->pk.row doubles, zeroed here) on
+// stream s: one persistent launch per angular-momentum class over all molecules' work items. The work
+// descriptors of every class are staged once; the call returns when the work is enqueued.
+void compute_three_center_grouped(const std::vector<df_handle*>& hs, const std::vector<double*>& outs,
+                                  cudaStream_t s) {
+    const int nmol = (int)hs.size();
+    if (nmol == 0) return;
+    const double* tab = rys_table_device();
+    int dev = 0, sms = 0;
+    DF_CUDA(cudaGetDevice(&dev));
+    DF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int i = 0; i < nmol; ++i)
+        DF_CUDA(cudaMemsetAsync(outs[i], 0, (size_t)hs[i]->naux * hs[i]->pk.row * sizeof(double), s));
+    constexpr int NCLS = (DF_LMAX_AUX + 1) * 6;   // (lP, la >= lb) classes
+    std::vector<Mol3c> mols((size_t)NCLS * nmol);
+    std::vector<long long> off((size_t)NCLS * (nmol + 1));
+    for (int lp = 0; lp <= DF_LMAX_AUX; ++lp)
+        for (int ci = 0; ci < 6; ++ci) {                  // pair_classes order: la ascending, lb <= la
+            const int k = lp * 6 + ci;
+            long long* o = &off[(size_t)k * (nmol + 1)];
+            o[0] = 0;
+            for (int i = 0; i < nmol; ++i) {
+                df_handle* h = hs[i];
+                const ClassList& c = h->pair_classes[ci];
+                const int na = (int)h->aux_by_l[lp].size();
+                mols[(size_t)k * nmol + i] = Mol3c{view(h->dbas), view(h->daux), c.d_pairs, c.count,
+                                                   h->d_aux_by_l[lp].p, na, outs[i], h->pk.row};
+                const long long items =
+                    (c.count > 0 && na > 0) ? (long long)((c.count + 127) / 128) * ((na + AUX_PER_ITEM - 1) / AUX_PER_ITEM)
+                                            : 0;
+                o[i + 1] = o[i] + items;
+            }
+        }
+    DevBuf<Mol3c> dmols;
+    DevBuf<long long> doff;
+    DevBuf<unsigned long long> dcounter;
+    dmols.alloc(mols.size());
+    doff.alloc(off.size());
+    dcounter.alloc(NCLS);
+    DF_CUDA(cudaMemcpyAsync(dmols.p, mols.data(), sizeof(Mol3c) * mols.size(), cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemsetAsync(dcounter.p, 0, sizeof(unsigned long long) * NCLS, s));
+    for (int lp = 0; lp <= DF_LMAX_AUX; ++lp)
+        for (int la = 0; la <= DF_LMAX_ORB; ++la)
+            for (int lb = 0; lb <= la; ++lb) {
+                const int k = lp * 6 + la * (la + 1) / 2 + lb;
+                const long long total = off[(size_t)k * (nmol + 1) + nmol];
+                if (total == 0) continue;
+                const unsigned grid = (unsigned)std::min<long long>(total, (long long)sms * 8);
+                const Mol3c* dm = dmols.p + (size_t)k * nmol;
+                const long long* doffk = doff.p + (size_t)k * (nmol + 1);
+#define G_CASE(P, A, B)                                                                                   \
+    if (lp == P && la == A && lb == B)                                                                    \
+        eri3c_grouped_kernel<P, A, B><<<grid, 128, 0, s>>>(dm, doffk, nmol, dcounter.p + k, tab);
+#define G_ROW(P) G_CASE(P, 0, 0) G_CASE(P, 1, 0) G_CASE(P, 1, 1) G_CASE(P, 2, 0) G_CASE(P, 2, 1) G_CASE(P, 2, 2)
+                G_ROW(0) G_ROW(1) G_ROW(2) G_ROW(3)
+#undef G_ROW
+#undef G_CASE
+                DF_CHECK_LAUNCH();
+            }
+    DF_CUDA(cudaStreamSynchronize(s));   // the staging buffers are released on return
 }
 
 }  // namespace dfhf

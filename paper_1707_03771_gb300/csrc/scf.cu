@@ -22,7 +22,6 @@ namespace dfhf {
 
 void jk_dispatch(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK, int precision,
                  int slices);
-void build_B(df_handle* h, double tau, bool keep, int whitening);
 void exchange_only(df_handle* h, const double* dC, int m, int precision, int slices, double* dK);
 
 namespace {
@@ -870,6 +869,10 @@ int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs
     }
     int status = DF_OK;
     try {
+        // the three-centre integrals of every molecule without B in one grouped launch per class; each
+        // molecule's metric factor and whitening follow when the driver starts it
+        build_B_batch(hs, nmol, o->screen_tau, false, o->precision == DF_PREC_FP64 ? DF_WHITEN_FP64 : DF_WHITEN_SPLIT,
+                      false);
         if (o->guess == DF_GUESS_SAD)
             for (int i = 0; i < nmol; ++i) {
                 int m0 = 0;

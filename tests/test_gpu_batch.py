@@ -57,3 +57,26 @@ def test_batch_rejects_duplicate_handles(lib):
         with pytest.raises(lib.DFError) as e:
             lib.scf_batch([h, h])
         assert e.value.code == lib.DF_E_ARG
+
+
+@pytest.mark.parametrize("whitening", [0, 1])
+def test_grouped_integrals_equal_single_builds(lib, whitening):
+    """df_build_B_batch (one persistent launch per class over all molecules' work items) gives bitwise the
+    integrals, and B, of each molecule's own df_build_B_ex; molecules of uneven size, several classes empty in
+    the smallest (one water has no d-d pairs across atoms of two waters)."""
+    systems = [clusters.water_cluster(w, 500 + w) for w in (3, 1, 5, 2)]
+    ref3, refB = [], []
+    for s in systems:
+        with lib.Handle(s) as h:
+            h.build_B(keep_3c=True, whitening=whitening)
+            ref3.append(h.rows(0, 0, h.naux))
+            refB.append(h.rows(1, 0, h.naux))
+    handles = [lib.Handle(s) for s in systems]
+    try:
+        lib.build_B_batch(handles, keep_3c=True, whitening=whitening)
+        for h, a, b in zip(handles, ref3, refB):
+            assert np.array_equal(h.rows(0, 0, h.naux), a)
+            assert np.array_equal(h.rows(1, 0, h.naux), b)
+    finally:
+        for h in handles:
+            h.close()
