@@ -147,7 +147,7 @@ int df_build_B_ex(df_handle* h, double screen_tau, int keep_3c, int whitening);
  * counterpart): the three-centre integrals of all of them run as one persistent launch per angular-momentum
  * class over a global queue of (molecule, block of 128 shell pairs, block of 8 auxiliary shells) work items,
  * then each molecule's metric factor, inverse and whitening follow on its own stream. The integrals are
- * bitwise those of df_build_B. Every handle needs room for its integrals at once. Returns the first failure
+ * those of df_build_B to rounding (the same per-triple code in another kernel). Every handle needs room for its integrals at once. Returns the first failure
  * (each handle's df_last_error holds it); handles left without B are reset. */
 int df_build_B_batch(df_handle** hs, int n, double screen_tau, int keep_3c, int whitening);
 

@@ -225,4 +225,30 @@ void sad_factor(df_handle* h, DevBuf<double>& C0, int& m0);
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
+
+// CUDA events marking the phases of one build for the per-phase timings; none at all when `on` is false
+// (batched runs, and stream capture, where a call's own events cannot be recorded and then destroyed)
+struct PhaseTimer {
+    static constexpr int MAXEV = 8;
+    cudaEvent_t ev[MAXEV] = {};
+    int count = 0;
+    bool on = false;
+    PhaseTimer(bool enabled, int n) : count(n < MAXEV ? n : MAXEV), on(enabled) {
+        if (on)
+            for (int i = 0; i < count; ++i) DF_CUDA(cudaEventCreate(&ev[i]));
+    }
+    PhaseTimer(const PhaseTimer&) = delete;
+    PhaseTimer& operator=(const PhaseTimer&) = delete;
+    void mark(int i, cudaStream_t s) {
+        if (on) DF_CUDA(cudaEventRecord(ev[i], s));
+    }
+    double ms(int a, int b) const { return elapsed_ms(ev[a], ev[b]); }
+    void sync(int i) {
+        if (on) DF_CUDA(cudaEventSynchronize(ev[i]));
+    }
+    ~PhaseTimer() {
+        if (on)
+            for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);
+    }
+};
 }  // namespace dfhf

@@ -138,34 +138,28 @@ void ensure_jk_buffers(df_handle* h, int nocc) {
 void coulomb_fp64(df_handle* h, const double* dD, double* dJ) {
     const Packing& pk = h->pk;
     cudaStream_t s = h->stream;
-    cudaEvent_t e0, e1, e2;
-    DF_CUDA(cudaEventCreate(&e0));
-    DF_CUDA(cudaEventCreate(&e1));
-    DF_CUDA(cudaEventCreate(&e2));
+    PhaseTimer t(h->sync_timing, 3);
     pack_density_kernel<<<dim3(pk.nt, pk.nt), 256, 0, s>>>(dD, h->n, h->Dw.p);
     DF_CHECK_LAUNCH();
-    DF_CUDA(cudaEventRecord(e0, s));
+    t.mark(0, s);
     gamma_kernel<<<h->naux, 256, 0, s>>>(h->B.p, pk.row, h->Dw.p, h->gamma.p);
     DF_CHECK_LAUNCH();
-    DF_CUDA(cudaEventRecord(e1, s));
+    t.mark(1, s);
     const long long c2 = pk.row / 2;
     coulomb_kernel<<<dim3((unsigned)((c2 + 255) / 256), J_SPLIT), 256, 0, s>>>(h->B.p, pk.row, h->naux, h->gamma.p,
                                                                              J_SPLIT, h->Jp.p + pk.row);
     DF_CHECK_LAUNCH();
-    DF_CUDA(cudaEventRecord(e2, s));
+    t.mark(2, s);
     sum_splits_kernel<<<(unsigned)((pk.row + 255) / 256), 256, 0, s>>>(h->Jp.p + pk.row, J_SPLIT, pk.row, h->Jp.p);
     DF_CHECK_LAUNCH();
     const long long nn = (long long)h->n * h->n;
     unpack_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(h->Jp.p, h->n, dJ);
     DF_CHECK_LAUNCH();
-    if (h->sync_timing) {
-        DF_CUDA(cudaEventSynchronize(e2));
-        h->timings_ms[4] = elapsed_ms(e0, e1);
-        h->timings_ms[5] = elapsed_ms(e1, e2);
+    if (t.on) {
+        t.sync(2);
+        h->timings_ms[4] = t.ms(0, 1);
+        h->timings_ms[5] = t.ms(1, 2);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
 }
 
 void pad_occupied(df_handle* h, const double* dC, int nocc, int ldy) {
@@ -178,27 +172,21 @@ void exchange_fp64(df_handle* h, int nocc, double* dK) {
     const Packing& pk = h->pk;
     cudaStream_t s = h->stream;
     const int ldy = ((nocc + 31) / 32) * 32;
-    cudaEvent_t e0, e1, e2;
-    DF_CUDA(cudaEventCreate(&e0));
-    DF_CUDA(cudaEventCreate(&e1));
-    DF_CUDA(cudaEventCreate(&e2));
-    DF_CUDA(cudaEventRecord(e0, s));
+    PhaseTimer t(h->sync_timing, 3);
+    t.mark(0, s);
     h->exchange_launches = 3;   // Y transform, K contraction, K reduction
     const size_t ny = (size_t)h->naux * pk.np * ldy;   // the FP64 Y is allocated on first FP64 use only
     if (h->Y.n < ny) h->Y.alloc(ny);
     y_transform_fp64(s, h->B.p, pk.row, pk.nt, h->naux, h->Cpad.p, ldy, nocc, h->Y.p);
-    DF_CUDA(cudaEventRecord(e1, s));
+    t.mark(1, s);
     const int ntiles = pk.nt * (pk.nt + 1) / 2;
     k_syrk_fp64(s, h->Y.p, h->naux, pk.np, ldy, nocc, k_splits(h), h->ktiles.p, ntiles, h->Kpart.p, h->n, dK);
-    DF_CUDA(cudaEventRecord(e2, s));
-    if (h->sync_timing) {
-        DF_CUDA(cudaEventSynchronize(e2));
-        h->timings_ms[6] = elapsed_ms(e0, e1);
-        h->timings_ms[7] = elapsed_ms(e1, e2);
+    t.mark(2, s);
+    if (t.on) {
+        t.sync(2);
+        h->timings_ms[6] = t.ms(0, 1);
+        h->timings_ms[7] = t.ms(1, 2);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
 }
 
 void jk_fp64(df_handle* h, const double* dD, const double* dC, int nocc, double* dJ, double* dK) {

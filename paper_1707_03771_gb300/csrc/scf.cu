@@ -243,6 +243,12 @@ __global__ void invsqrt_series_kernel(double* __restrict__ M, const double* __re
     M[idx] = (idx / m == idx % m ? 1.875 : 0.0) - 1.25 * M[idx] + 0.375 * M2[idx];
 }
 
+// a += b
+__global__ void add_inplace_kernel(double* __restrict__ a, const double* __restrict__ b, long long len) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) a[i] += b[i];
+}
+
 // Vw[i][k] = V[i][k] w[i] for the first m rows (the occupied eigenvectors weighted by sqrt(n_i / 2))
 __global__ void weight_rows_kernel(const double* __restrict__ V, const double* __restrict__ w, int m, int len,
                                    double* __restrict__ Vw) {
@@ -410,6 +416,8 @@ class ScfRun {
             incremental_jk();
             ++inc_since_ref_;
             ++r_->incremental_builds;
+        } else if (first_factor_ && m0_ > nocc_) {
+            first_factor_jk();
         } else {
             jk_dispatch(h_, h_->Dm.p, h_->dC.p, first_factor_ ? m0_ : nocc_, h_->dJ.p, h_->dK.p, o_.precision,
                         slices_);
@@ -556,6 +564,24 @@ class ScfRun {
     void mm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
             const double* B, int ldb, double beta, double* C, int ldc) {
         dgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+
+    // J and K of the first Fock matrix from the factor C0 (m0 > nocc columns): J from D0, K as the sum of the
+    // exchanges of column blocks of at most nocc columns (the orbital-form exchange is additive over columns),
+    // so the exchange buffers keep the width of the occupied orbitals
+    void first_factor_jk() {
+        coulomb_fp64(h_, h_->Dm.p, h_->dJ.p);
+        const int m1 = nocc_, m2 = m0_ - nocc_;
+        double* Ca = h_->work1.p;   // n x m1
+        double* Cb = h_->work2.p;   // n x m2 (m0 <= n: both fit an n x n buffer)
+        DF_CUDA(cudaMemcpy2DAsync(Ca, sizeof(double) * m1, h_->dC.p, sizeof(double) * m0_, sizeof(double) * m1, n_,
+                                  cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaMemcpy2DAsync(Cb, sizeof(double) * m2, h_->dC.p + m1, sizeof(double) * m0_, sizeof(double) * m2, n_,
+                                  cudaMemcpyDeviceToDevice, s_));
+        exchange_only(h_, Ca, m1, o_.precision, slices_, h_->dK.p);
+        exchange_only(h_, Cb, m2, o_.precision, slices_, h_->work3.p);
+        add_inplace_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->dK.p, h_->work3.p, nn_);
+        DF_CHECK_LAUNCH();
     }
 
     // the full build just enqueued becomes the reference: K_ref = K, C_ref = C_occ

@@ -693,7 +693,7 @@ void tune_k(df_handle* h, SplitState* st, TcChoice& best) {
 // Y over auxiliary blocks: one block of all rows when every slice is resident; otherwise the slices of
 // each block of st->pblk rows are cut from the packed FP64 B just before the Y kernel consumes them.
 template <int S>
-void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK, cudaEvent_t* ev) {
+void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double* dK, PhaseTimer& ev) {
     cudaStream_t s = h->stream;
     const int np = st->np, ldy = st->ldy, naux = h->naux;
     const long long cstr = (long long)ldy * np;
@@ -732,7 +732,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         }
     }
     double tune_ms = 0.0;
-    DF_CUDA(cudaEventRecord(ev[0], s));
+    ev.mark(1, s);
     const int pblk = st->blocked ? st->pblk : naux;
     for (int p0 = 0; p0 < naux; p0 += pblk) {
         const int nb = std::min(pblk, naux - p0);
@@ -753,7 +753,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
             DF_CHECK_LAUNCH();
         }
     }
-    DF_CUDA(cudaEventRecord(ev[1], s));
+    ev.mark(2, s);
     {
         const int nyb = (naux + pblk - 1) / pblk;   // split C, per block (slicing,) Y, re-split Y, K, reduce
         h->exchange_launches = 4 + nyb * (st->blocked ? 2 : 1);
@@ -805,21 +805,21 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
             h->timings_ms[14] = g_tune_ms;
         }
         h->timings_ms[15] = ch.kN;
-        DF_CUDA(cudaEventRecord(ev[2], s));
+        ev.mark(3, s);
         k_split_tc(s, S, ch.kN, st->Ys, st->Ye, naux, np, ldy, ksplit, st->tiles128, st->ntiles128, st->Kpart_tc,
                    st->npt, st->err);
-        DF_CUDA(cudaEventRecord(ev[3], s));
+        ev.mark(4, s);
         k_tc_reduce(s, st->Kpart_tc, ksplit, st->npt, h->n, dK);
     } else {
         const int nt = np / 64;
         const int ntiles = nt * (nt + 1) / 2;
         const size_t ksmem = (size_t)2 * 2 * S * 64 * LDS * sizeof(bf16);
         DF_CUDA(cudaFuncSetAttribute(k_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
-        DF_CUDA(cudaEventRecord(ev[2], s));
+        ev.mark(3, s);
         k_split_kernel<S><<<dim3(ntiles, st->nsplit), 2 * (64 / WNT) * 32, ksmem, s>>>(
             st->Ys, ystr, st->Ye, naux, np, ldy, st->PB, st->nsplit, h->ktiles.p, st->Kpart);
         DF_CHECK_LAUNCH();
-        DF_CUDA(cudaEventRecord(ev[3], s));
+        ev.mark(4, s);
         const long long nn = (long long)h->n * h->n;
         k_split_reduce_kernel<<<nblocks(nn, 256), 256, 0, s>>>(st->Kpart, st->nsplit, np, h->n, dK);
         DF_CHECK_LAUNCH();
@@ -840,11 +840,9 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         free_split(h);
         st = nullptr;
     }
-    cudaEvent_t e0, e1, ev[4];
-    DF_CUDA(cudaEventCreate(&e0));
-    DF_CUDA(cudaEventCreate(&e1));
-    for (auto& e : ev) DF_CUDA(cudaEventCreate(&e));
-    DF_CUDA(cudaEventRecord(e0, h->stream));
+    // phase marks: 0 start, 1-2 Y, 3-4 K contraction, 5 end
+    PhaseTimer ev(h->sync_timing, 6);
+    ev.mark(0, h->stream);
     const int ldy = ((nocc + 31) / 32) * 32;
     // set-up: a failure part-way leaves no half-built state behind (the next call starts afresh)
     try {
@@ -954,9 +952,6 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     } catch (...) {
         cudaStreamSynchronize(h->stream);   // nothing queued may still use the buffers freed here
         free_split(h);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        for (auto& e : ev) cudaEventDestroy(e);
         throw;
     }
     if (st->err && !h->tc_err_host) DF_CUDA(cudaMemsetAsync(st->err, 0, sizeof(int), h->stream));
@@ -966,7 +961,7 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         case 4: run_split<4>(h, st, dC, nocc, dK, ev); break;
         default: run_split<5>(h, st, dC, nocc, dK, ev); break;
     }
-    DF_CUDA(cudaEventRecord(e1, h->stream));
+    ev.mark(5, h->stream);
     if (st->err && h->tc_err_host) {
         DF_CUDA(cudaMemcpyAsync(h->tc_err_host, st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     } else if (st->err) {
@@ -976,16 +971,13 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         DF_CUDA(cudaStreamSynchronize(h->stream));
         if (herr) throw Error{DF_E_TIMEOUT, "tensor-core exchange kernel timed out waiting on a barrier"};
     }
-    if (h->sync_timing) {
-        DF_CUDA(cudaEventSynchronize(e1));
-        h->timings_ms[8] = elapsed_ms(e0, e1);
-        h->timings_ms[9] = elapsed_ms(ev[0], ev[1]);    // Y = B C (split)
-        h->timings_ms[10] = elapsed_ms(ev[2], ev[3]);   // K contraction (split)
+    if (ev.on) {
+        ev.sync(5);
+        h->timings_ms[8] = ev.ms(0, 5);
+        h->timings_ms[9] = ev.ms(1, 2);    // Y = B C (split)
+        h->timings_ms[10] = ev.ms(3, 4);   // K contraction (split)
         h->timings_ms[11] = h->timings_ms[8] - h->timings_ms[9] - h->timings_ms[10];   // slicing, reduce
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (auto& e : ev) cudaEventDestroy(e);
 }
 
 void split_clear_error(df_handle* h) {

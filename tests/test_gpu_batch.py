@@ -61,9 +61,10 @@ def test_batch_rejects_duplicate_handles(lib):
 
 @pytest.mark.parametrize("whitening", [0, 1])
 def test_grouped_integrals_equal_single_builds(lib, whitening):
-    """df_build_B_batch (one persistent launch per class over all molecules' work items) gives bitwise the
-    integrals, and B, of each molecule's own df_build_B_ex; molecules of uneven size, several classes empty in
-    the smallest (one water has no d-d pairs across atoms of two waters)."""
+    """df_build_B_batch (one persistent launch per class over all molecules' work items) gives the integrals,
+    and B, of each molecule's own df_build_B_ex to rounding: both kernels run the same per-triple code, which
+    the compiler may contract into fused multiply-adds differently in the two kernels; molecules of uneven
+    size."""
     systems = [clusters.water_cluster(w, 500 + w) for w in (3, 1, 5, 2)]
     ref3, refB = [], []
     for s in systems:
@@ -75,8 +76,8 @@ def test_grouped_integrals_equal_single_builds(lib, whitening):
     try:
         lib.build_B_batch(handles, keep_3c=True, whitening=whitening)
         for h, a, b in zip(handles, ref3, refB):
-            assert np.array_equal(h.rows(0, 0, h.naux), a)
-            assert np.array_equal(h.rows(1, 0, h.naux), b)
+            assert np.abs(h.rows(0, 0, h.naux) - a).max() <= 1e-14 * np.abs(a).max()
+            assert np.abs(h.rows(1, 0, h.naux) - b).max() <= 1e-12 * np.abs(b).max()
     finally:
         for h in handles:
             h.close()
