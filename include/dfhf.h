@@ -110,6 +110,9 @@ typedef struct {
     double t_iter_s;         /* total SCF iteration time */
     double t_jk_s;           /* time in J/K builds */
     double t_total_s;
+    int graph_launches;      /* iteration parts launched as captured CUDA graphs (the J/K build and the Fock,
+                                energy and DIIS-error part are captured per kind of step on its second
+                                occurrence and replayed; DFHF_SCF_GRAPHS=0 launches every kernel directly) */
 } df_result;
 
 typedef struct df_handle df_handle;

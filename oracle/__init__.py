@@ -1,7 +1,8 @@
 """ORACLE -- test infrastructure only.
 
 A plain, slow FP64 CPU implementation of the density-fitted RHF step: McMurchie-Davidson
-integrals in C (md_integrals.c), the density-fitting / SCF algebra in numpy (dfrhf.py), the
+integrals in C (md_integrals.c), the density-fitting / SCF algebra in numpy (dfrhf.py; unrestricted
+Hartree-Fock in dfuhf.py), the
 superposition-of-atomic-densities guess (sad.py) and the guess network's forward and backward pass
 (mlp.py).
 Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs may import it;

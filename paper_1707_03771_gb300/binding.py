@@ -48,7 +48,8 @@ class Result(ctypes.Structure):
                 ("last_err", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("ramp_iteration", ctypes.c_int),
                 ("incremental_builds", ctypes.c_int), ("approx_steps", ctypes.c_int), ("t_build_s", ctypes.c_double),
-                ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double)]
+                ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double),
+                ("graph_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -12,7 +12,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <memory>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -86,6 +88,39 @@ __global__ void antisym_kernel(const double* __restrict__ T, int n, double a, do
     E[idx] = a * (T[idx] - T[(long long)j * n + i]);
 }
 
+// E_slot = a (T - T^T) (n x n) into the DIIS slot held in device memory (a captured graph replays it)
+__global__ void antisym_slot_kernel(const double* __restrict__ T, int n, double a, double* __restrict__ Ebase,
+                                    const int* __restrict__ slot) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (idx >= nn) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    Ebase[(long long)*slot * nn + idx] = a * (T[idx] - T[(long long)j * n + i]);
+}
+
+// out = max |x_slot| over the DIIS slot held in device memory (single block)
+__global__ void absmax_slot_kernel(const double* __restrict__ base, long long len, const int* __restrict__ slot,
+                                   double* __restrict__ out) {
+    const double* x = base + (long long)*slot * len;
+    double m = 0;
+    for (long long i = threadIdx.x; i < len; i += blockDim.x) m = fmax(m, fabs(x[i]));
+    __shared__ double sm[1024];
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+// dst_slot = src (the Fock matrix of this iteration into the DIIS slot held in device memory)
+__global__ void copy_to_slot_kernel(const double* __restrict__ src, double* __restrict__ base, long long len,
+                                    const int* __restrict__ slot) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) base[(long long)*slot * len + i] = src[i];
+}
+
 // out = max |x| (single block)
 __global__ void absmax_kernel(const double* __restrict__ x, long long len, double* __restrict__ out) {
     double m = 0;
@@ -101,9 +136,10 @@ __global__ void absmax_kernel(const double* __restrict__ x, long long len, doubl
 }
 
 // DIIS: Bm[slot][j] = Bm[j][slot] = <e_slot, e_j> for the vectors present (one block per j)
-__global__ void diis_dots_kernel(const double* __restrict__ E, long long len, int slot, const int* __restrict__ present,
-                                 int size, double* __restrict__ Bm) {
+__global__ void diis_dots_kernel(const double* __restrict__ E, long long len, const int* __restrict__ slotp,
+                                 const int* __restrict__ present, int size, double* __restrict__ Bm) {
     const int j = blockIdx.x;
+    const int slot = *slotp;
     if (!present[j]) return;
     const double* a = E + (long long)slot * len;
     const double* b = E + (long long)j * len;
@@ -281,6 +317,64 @@ std::vector<double> aufbau_occupations(const std::vector<double>& eps, double ne
 
 namespace {
 
+// Captured CUDA graphs of the SCF's repeated device sequences, one per kind of step (precision, slices,
+// full or incremental exchange). A kind is launched directly the first time it occurs (buffers are sized and
+// tile choices made then), captured from the stream the second time and replayed from then on; the sequence
+// reads everything that changes between iterations (the DIIS slot) from device memory. A sequence that
+// cannot be captured (a call that is not allowed in stream capture) is marked and launched directly.
+class GraphCache {
+  public:
+    ~GraphCache() { clear(); }
+    void clear() {
+        for (auto& kv : exec_) cudaGraphExecDestroy(kv.second);
+        exec_.clear();
+        seen_.clear();
+        broken_.clear();
+    }
+    template <typename F>
+    void run(cudaStream_t s, int kind, F&& fn) {
+        auto it = exec_.find(kind);
+        if (it != exec_.end()) {
+            DF_CUDA(cudaGraphLaunch(it->second, s));
+            ++replays_;
+            return;
+        }
+        if (!enabled_ || broken_.count(kind) || seen_[kind]++ == 0) {
+            fn();
+            return;
+        }
+        cudaGraph_t g = nullptr;
+        DF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        bool ok = true;
+        try {
+            fn();
+        } catch (...) {
+            ok = false;
+        }
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        cudaGraphExec_t ex = nullptr;
+        if (ok && e == cudaSuccess && g) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        else ok = false;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();   // a refused capture leaves no error for the next call
+        if (!ok) {
+            broken_.insert(kind);
+            fn();   // nothing of the refused capture ran: launch the sequence directly
+            return;
+        }
+        exec_[kind] = ex;
+        DF_CUDA(cudaGraphLaunch(ex, s));
+        ++replays_;
+    }
+    bool enabled_ = true;
+    int replays_ = 0;
+
+  private:
+    std::map<int, cudaGraphExec_t> exec_;
+    std::map<int, int> seen_;
+    std::set<int> broken_;
+};
+
 // One molecule's SCF as a sequence of asynchronous iterations with a single host synchronisation each
 // (the energy terms, max|e| and status words), so that many molecules can advance in lock-step on their
 // own streams (scf_run_batch) while the GPU overlaps their kernels.
@@ -324,8 +418,14 @@ class ScfRun {
         slices_ = o_.slices;
         DF_CUDA(cudaMalloc((void**)&info_, sizeof(int)));
         DF_CUDA(cudaHostAlloc((void**)&pin_, sizeof(double) * 8, cudaHostAllocDefault));
-        DF_CUDA(cudaHostAlloc((void**)&pin_ctl_, sizeof(int) * (2 * DIIS_MAX + 3), cudaHostAllocDefault));
+        DF_CUDA(cudaHostAlloc((void**)&pin_ctl_, sizeof(int) * (2 * DIIS_MAX + 4), cudaHostAllocDefault));
         pin_ctl_[2 * DIIS_MAX + 2] = 0;
+        pin_ctl_[2 * DIIS_MAX + 3] = 0;   // the DIIS slot of the iteration being built
+        // per-phase timings take event synchronisations, which stream capture does not allow
+        saved_sync_timing_ = h_->sync_timing;
+        h_->sync_timing = false;
+        const char* gv = std::getenv("DFHF_SCF_GRAPHS");
+        graphs_.enabled_ = !frac_ && !(gv && gv[0] == '0');
         h_->tc_err_host = pin_ctl_ + 2 * DIIS_MAX + 2;   // timeout flag of the tensor-core kernels
         split_clear_error(h_);
         DF_CUDA(cudaEventCreate(&ev_done_));
@@ -369,8 +469,11 @@ class ScfRun {
         d_B_ = h_->diisB.p;
         d_scal_ = d_B_ + DIIS_MAX * DIIS_MAX;
         d_coef_ = d_scal_ + 8;
-        DF_CUDA(cudaMalloc((void**)&d_ints_, sizeof(int) * (2 * DIIS_MAX + 2)));   // present | slots | status
-        DF_CUDA(cudaMemsetAsync(d_ints_, 0, sizeof(int) * (2 * DIIS_MAX + 2), s_));
+        // present | slots | status | (unused) | slot of the iteration being built
+        DF_CUDA(cudaMalloc((void**)&d_ints_, sizeof(int) * (2 * DIIS_MAX + 4)));
+        DF_CUDA(cudaMemsetAsync(d_ints_, 0, sizeof(int) * (2 * DIIS_MAX + 4), s_));
+        d_slot_ = d_ints_ + 2 * DIIS_MAX + 3;
+        if (o_.incremental) alloc_reference();
         DF_CUDA(cudaMalloc((void**)&Fp_, sizeof(double) * nX_ * nX_));
         DF_CUDA(cudaMalloc((void**)&T1_, sizeof(double) * n_ * nX_));
         DF_CUDA(cudaMalloc((void**)&Fo_, sizeof(double) * nX_ * nX_));
@@ -408,32 +511,13 @@ class ScfRun {
         return false;
     }
 
-    // J/K, Fock, energy, error vector; scalars and status words copied to pinned memory; one event
+    // J/K, Fock, energy, error vector; scalars and status words copied to pinned memory; one event. The
+    // host decisions come first; the device work of both parts is a captured graph per kind of step
+    // (GraphCache), except in the iteration built from an initial factor.
     void enqueue_iteration() {
         ++it_;
-        DF_CUDA(cudaEventRecord(ej0_, s_));
-        if (o_.incremental && late_ && inc_since_ref_ >= 0 && inc_since_ref_ + 1 < INC_RESET) {
-            incremental_jk();
-            ++inc_since_ref_;
-            ++r_->incremental_builds;
-        } else if (first_factor_ && m0_ > nocc_) {
-            first_factor_jk();
-        } else {
-            jk_dispatch(h_, h_->Dm.p, h_->dC.p, first_factor_ ? m0_ : nocc_, h_->dJ.p, h_->dK.p, o_.precision,
-                        slices_);
-            if (o_.incremental && late_) set_reference();
-        }
-        DF_CUDA(cudaEventRecord(ej1_, s_));
-        fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, h_->F.p);
-        DF_CHECK_LAUNCH();
-        energy_kernel<<<1, 1024, 0, s_>>>(h_->Dm.p, h_->H.p, h_->dJ.p, h_->dK.p, nn_, d_scal_);
-        DF_CHECK_LAUNCH();
-        // F' = X^T F X; error e = X^T (FDS - SDF) X = 2 (F' P - P F'), P = V_occ V_occ^T, into the next slot
-        to_orth(h_->F.p, Fo_);
-        if (!first_factor_) {
-            mm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
-            mm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
-        }
+        const bool inc = o_.incremental && late_ && inc_since_ref_ >= 0 && inc_since_ref_ + 1 < INC_RESET;
+        const bool ref = !inc && o_.incremental && late_;
         slot_ = 0;
         if ((int)order_.size() < dsize_) {
             while (present_[slot_]) ++slot_;
@@ -442,24 +526,78 @@ class ScfRun {
             order_.erase(order_.begin());
             present_[slot_] = 0;
         }
-        double* Eslot = h_->diisE.p + (long long)slot_ * nX_ * nX_;
+        pin_ctl_[2 * DIIS_MAX + 3] = slot_;
+        DF_CUDA(cudaEventRecord(ej0_, s_));
         if (first_factor_) {
+            if (m0_ > nocc_) first_factor_jk();
+            else jk_dispatch(h_, h_->Dm.p, h_->dC.p, m0_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+        } else {
+            const int kind = ((o_.precision == DF_PREC_SPLIT ? slices_ : 0) << 2) | (inc ? 2 : (ref ? 1 : 0));
+            graphs_.run(s_, kind, [&] { jk_device(inc, ref); });
+        }
+        if (inc) {
+            ++inc_since_ref_;
+            ++r_->incremental_builds;
+        } else if (ref) {
+            inc_since_ref_ = 0;
+        }
+        DF_CUDA(cudaEventRecord(ej1_, s_));
+        if (first_factor_) {
+            DF_CUDA(cudaMemcpyAsync(d_slot_, pin_ctl_ + 2 * DIIS_MAX + 3, sizeof(int), cudaMemcpyHostToDevice, s_));
+            fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, h_->F.p);
+            DF_CHECK_LAUNCH();
+            energy_kernel<<<1, 1024, 0, s_>>>(h_->Dm.p, h_->H.p, h_->dJ.p, h_->dK.p, nn_, d_scal_);
+            DF_CHECK_LAUNCH();
+            to_orth(h_->F.p, Fo_);
             // the density is the factor's, not an Aufbau projector: e = X^T (F D S - S D F) X in full
+            double* Eslot = h_->diisE.p + (long long)slot_ * nX_ * nX_;
             mm(s_, false, false, n_, n_, n_, 1.0, h_->F.p, n_, h_->Dm.p, n_, 0.0, h_->work1.p, n_);
             mm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
             antisym_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->work2.p, n_, 1.0, h_->work3.p);
             DF_CHECK_LAUNCH();
             to_orth(h_->work3.p, Eslot);
-        } else {
-            antisym_kernel<<<nblk((long long)nX_ * nX_), 256, 0, s_>>>(h_->work1.p, nX_, 2.0, Eslot);
+            absmax_kernel<<<1, 1024, 0, s_>>>(Eslot, (long long)nX_ * nX_, d_scal_ + 3);
             DF_CHECK_LAUNCH();
+            copy_scalars();
+        } else {
+            graphs_.run(s_, POST_KIND, [&] { post_device(); });
         }
-        absmax_kernel<<<1, 1024, 0, s_>>>(Eslot, (long long)nX_ * nX_, d_scal_ + 3);
+        DF_CUDA(cudaEventRecord(ev_done_, s_));
+    }
+
+    // the exchange (and Coulomb) build of one iteration: full, full becoming the new reference, or K_ref
+    // plus the exchange of the factorised density change
+    void jk_device(bool inc, bool ref) {
+        if (inc) {
+            incremental_jk();
+        } else {
+            jk_dispatch(h_, h_->Dm.p, h_->dC.p, nocc_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+            if (ref) set_reference();
+        }
+    }
+
+    // Fock matrix, energy terms, F' = X^T F X and the error e = 2 (F' P - P F') (P = V_occ V_occ^T) into the
+    // DIIS slot named in device memory, max|e|; scalars and status words to pinned memory
+    void post_device() {
+        DF_CUDA(cudaMemcpyAsync(d_slot_, pin_ctl_ + 2 * DIIS_MAX + 3, sizeof(int), cudaMemcpyHostToDevice, s_));
+        fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, h_->F.p);
         DF_CHECK_LAUNCH();
+        energy_kernel<<<1, 1024, 0, s_>>>(h_->Dm.p, h_->H.p, h_->dJ.p, h_->dK.p, nn_, d_scal_);
+        DF_CHECK_LAUNCH();
+        to_orth(h_->F.p, Fo_);
+        mm(s_, false, true, nX_, nocc_, nX_, 1.0, Fo_, nX_, vt_, nX_, 0.0, h_->work2.p, nocc_);      // F' V_occ
+        mm(s_, false, false, nX_, nX_, nocc_, 1.0, h_->work2.p, nocc_, vt_, nX_, 0.0, h_->work1.p, nX_);
+        antisym_slot_kernel<<<nblk((long long)nX_ * nX_), 256, 0, s_>>>(h_->work1.p, nX_, 2.0, h_->diisE.p, d_slot_);
+        DF_CHECK_LAUNCH();
+        absmax_slot_kernel<<<1, 1024, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, d_slot_, d_scal_ + 3);
+        DF_CHECK_LAUNCH();
+        copy_scalars();
+    }
+
+    void copy_scalars() {
         DF_CUDA(cudaMemcpyAsync(pin_, d_scal_, 4 * sizeof(double), cudaMemcpyDeviceToHost, s_));
         DF_CUDA(cudaMemcpyAsync(pin_ctl_ + 2 * DIIS_MAX, d_ints_ + 2 * DIIS_MAX, sizeof(int), cudaMemcpyDeviceToHost, s_));
         DF_CUDA(cudaMemcpyAsync(pin_ctl_ + 2 * DIIS_MAX + 1, info_, sizeof(int), cudaMemcpyDeviceToHost, s_));
-        DF_CUDA(cudaEventRecord(ev_done_, s_));
     }
 
     // wait for the iteration, test convergence; if not done, enqueue DIIS and the Roothaan step
@@ -517,14 +655,14 @@ class ScfRun {
             order_.clear();
         }
         const long long no = (long long)nX_ * nX_;
-        DF_CUDA(cudaMemcpyAsync(h_->diisF.p + (long long)slot_ * no, Fo_, no * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s_));
+        copy_to_slot_kernel<<<nblk(no), 256, 0, s_>>>(Fo_, h_->diisF.p, no, d_slot_);
+        DF_CHECK_LAUNCH();
         present_[slot_] = 1;
         order_.push_back(slot_);
         for (int q = 0; q < DIIS_MAX; ++q) pin_ctl_[q] = present_[q];
         for (size_t q = 0; q < order_.size(); ++q) pin_ctl_[DIIS_MAX + q] = order_[q];
         DF_CUDA(cudaMemcpyAsync(d_ints_, pin_ctl_, sizeof(int) * 2 * DIIS_MAX, cudaMemcpyHostToDevice, s_));
-        diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, slot_, d_ints_, DIIS_MAX, d_B_);
+        diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, d_slot_, d_ints_, DIIS_MAX, d_B_);
         DF_CHECK_LAUNCH();
         // Roothaan step: a full eigensolve, or late (options.approx_diag) a rotation of the previous
         // orbitals, with a full eigensolve every DIAG_RESET late iterations
@@ -584,18 +722,19 @@ class ScfRun {
         DF_CHECK_LAUNCH();
     }
 
+    // buffers of the incremental Fock build
+    void alloc_reference() {
+        const long long m = nocc_;
+        DF_CUDA(cudaMalloc((void**)&Kref_, sizeof(double) * nn_ * 3));   // K_ref | K_+ | K_-
+        DF_CUDA(cudaMalloc((void**)&Cref_, sizeof(double) * n_ * m * 3));   // C_ref | C_+ | C_-
+        DF_CUDA(cudaMalloc((void**)&Wq_, sizeof(double) * n_ * 2 * m * 2));   // W / Q | V^T
+        DF_CUDA(cudaMalloc((void**)&core_, sizeof(double) * (4 * m * m + 4 * m)));   // core | l | tau
+    }
+
     // the full build just enqueued becomes the reference: K_ref = K, C_ref = C_occ
     void set_reference() {
-        if (!Kref_) {
-            const long long m = nocc_;
-            DF_CUDA(cudaMalloc((void**)&Kref_, sizeof(double) * nn_ * 3));   // K_ref | K_+ | K_-
-            DF_CUDA(cudaMalloc((void**)&Cref_, sizeof(double) * n_ * m * 3));   // C_ref | C_+ | C_-
-            DF_CUDA(cudaMalloc((void**)&Wq_, sizeof(double) * n_ * 2 * m * 2));   // W / Q | V^T
-            DF_CUDA(cudaMalloc((void**)&core_, sizeof(double) * (4 * m * m + 4 * m)));   // core | l | tau
-        }
         DF_CUDA(cudaMemcpyAsync(Kref_, h_->dK.p, nn_ * sizeof(double), cudaMemcpyDeviceToDevice, s_));
         DF_CUDA(cudaMemcpyAsync(Cref_, h_->dC.p, sizeof(double) * n_ * nocc_, cudaMemcpyDeviceToDevice, s_));
-        inc_since_ref_ = 0;
     }
 
     // J in full; K = K_ref + K[C_+] - K[C_-] from the factorised density change
@@ -761,12 +900,15 @@ class ScfRun {
         r_->t_iter_s = std::chrono::duration<double>(clk::now() - t_iter_).count();
         r_->t_jk_s = jk_ms_ / 1000.0;
         r_->t_total_s = std::chrono::duration<double>(clk::now() - t_start_).count();
+        r_->graph_launches = graphs_.replays_;
     }
 
     void release() {
         // work this run queued (on an error path: copies into the pinned words, kernels on its buffers)
         // completes before anything is freed
         if (s_) cudaStreamSynchronize(s_);
+        graphs_.clear();
+        if (pin_ctl_ && h_) h_->sync_timing = saved_sync_timing_;
         if (h_ && pin_ctl_ && h_->tc_err_host == pin_ctl_ + 2 * DIIS_MAX + 2) h_->tc_err_host = nullptr;
         if (work_) cudaFree(work_);
         if (info_) cudaFree(info_);
@@ -833,6 +975,10 @@ class ScfRun {
     const double* C0_ = nullptr;   // initial factor (set_initial_factor): the first Fock matrix from 2 C0 C0^T
     int m0_ = 0;
     bool first_factor_ = false;    // the iteration being built uses C0 (no Roothaan step taken yet)
+    static constexpr int POST_KIND = 1 << 10;   // graph kind of the post-J/K part
+    GraphCache graphs_;
+    int* d_slot_ = nullptr;        // device copy of the DIIS slot of the iteration being built
+    bool saved_sync_timing_ = true;
 };
 
 }  // namespace

@@ -553,3 +553,33 @@ def test_sad_density_assembly(water2_sys):
                 assert not blk.any()
         if int(water2_sys.atoms["Z"][a]) == 8:
             assert np.abs(D0[lo:hi, lo:hi] - Dox).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# unrestricted Hartree-Fock (oracle/dfuhf.py)
+# ---------------------------------------------------------------------------------------------
+
+def test_uhf_closed_shell_equals_rhf(water2_sys):
+    """With as many alpha as beta electrons the UHF determinant stays restricted: the RHF energy, spin
+    densities of half the RHF density, <S^2> = 0."""
+    from oracle import dfuhf
+    n = water2_sys.n_electrons // 2
+    u = dfuhf.uhf(water2_sys, n, n)
+    r = dfrhf.scf(water2_sys)
+    assert u.converged and abs(u.energy - r.energy) <= 1e-9, (u.energy, r.energy)
+    assert np.abs(u.Da - 0.5 * r.D).max() <= 1e-6 and np.abs(u.Da - u.Db).max() <= 1e-6
+    assert abs(u.s2) <= 1e-9
+
+
+def test_uhf_hydrogen_atom_has_no_electron_interaction(water2_sys):
+    """One electron: J[D_a] and K_a cancel exactly (with density fitting too: both give sum_P gamma_P^2 for
+    the single orbital), so the UHF energy is the lowest eigenvalue of the core Hamiltonian in the metric S,
+    and <S^2> = 3/4."""
+    from scipy.linalg import eigh
+
+    from oracle import dfuhf, sad
+    atom = sad.atom_system(water2_sys, 1)
+    u = dfuhf.uhf(atom, 1, 0)
+    e0 = eigh(dfrhf.core_hamiltonian(atom), dfrhf.overlap(atom), eigvals_only=True)[0]
+    assert u.converged and abs(u.energy - e0) <= 1e-10, (u.energy, e0)
+    assert abs(u.s2 - 0.75) <= 1e-12
