@@ -110,6 +110,7 @@ typedef struct {
     double t_iter_s;         /* total SCF iteration time */
     double t_jk_s;           /* time in J/K builds */
     double t_total_s;
+    double s2;               /* <S^2> of the determinant (scf_run_uhf; 0 for RHF) */
     int graph_launches;      /* iteration parts launched as captured CUDA graphs (the J/K build and the Fock,
                                 energy and DIIS-error part are captured per kind of step on its second
                                 occurrence and replayed; DFHF_SCF_GRAPHS=0 launches every kernel directly) */
@@ -123,6 +124,12 @@ typedef struct df_handle df_handle;
  * Returns DF_E_ARG for invalid shells (exponent <= 0, l out of range) or an odd electron count. */
 int df_init(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh,
             const df_shell* aux, int naux_sh, int charge, df_handle** out);
+
+/* As df_init, but any electron count >= 1 is accepted (open-shell systems for scf_run_uhf). A handle with an
+ * odd electron count is refused by the restricted entry points (scf_run, scf_run_guess, scf_run_batch:
+ * DF_E_STATE); its nocc is ceil(N / 2). */
+int df_init_open(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh,
+                 const df_shell* aux, int naux_sh, int charge, df_handle** out);
 
 /* Sizes: n orbital functions, naux auxiliary functions, nocc doubly occupied orbitals, and the
  * length of one packed row of B (doubles). Any pointer may be NULL. */
@@ -190,6 +197,17 @@ int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* o
  * DF_E_NUMERIC if an atomic SCF does not converge. */
 int df_sad_density(df_handle* h, double* D0);
 
+/* Unrestricted Hartree-Fock with nalpha and nbeta electrons (paper, section "Program features", "Standard
+ * algorithms": UHF on the density-fitted Fock builder): spin densities D_s = C_s C_s^T, J from D_a + D_b,
+ * K_s = sum_{P, i in s} Y Y^T from each spin's occupied orbitals (FP64, or split precision: 3 slices until
+ * max|e| < 1e-4, then 5, converging only on the 5-slice builds), F_s = H + J - K_s,
+ * E = 1/2 tr(D_a(H + F_a)) + 1/2 tr(D_b(H + F_b)) + E_nuc, Pulay DIIS over the pair of orthogonal-basis Fock
+ * matrices with errors X^T(F_s D_s S - S D_s F_s)X, core-Hamiltonian start for both spins, convergence as
+ * scf_run on the larger of the two errors. out->s2 = <S^2>. Requires nalpha >= nbeta >= 0 and
+ * nalpha + nbeta = electron count (DF_E_ARG otherwise); options.guess must be DF_GUESS_CORE, incremental and
+ * approx_diag 0. After the run df_get_matrix gives the total density (6) and the spin densities (12, 13). */
+int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_result* out);
+
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
  * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric
  * (eigenvectors of X^T S D0 S X). Otherwise as scf_run. */
@@ -242,7 +260,8 @@ int df_scf_history(const df_handle* h, double* out, int max_rows);
 int df_get_rows(df_handle* h, int which, int p0, int count, double* out);
 
 /* Copy a matrix to host: 0 S, 1 T, 2 V, 3 H, 4 metric (naux x naux), 5 L^-1 (naux x naux, lower),
- * 6 D, 7 F, 8 J, 9 K (last SCF iteration), 10 C (n x n, columns = orbitals), 11 orbital energies (n). */
+ * 6 D, 7 F, 8 J, 9 K (last SCF iteration), 10 C (n x n, columns = orbitals), 11 orbital energies (n),
+ * 12 and 13 the alpha and beta densities of the last scf_run_uhf. */
 int df_get_matrix(df_handle* h, int which, double* out);
 
 /* Rys quadrature nodes x (= t^2) and weights w for `count` arguments T (host arrays; x and w are

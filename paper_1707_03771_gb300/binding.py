@@ -22,7 +22,8 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_coulomb_noalloc", "df_scf_history", "scf_run_batch", "scf_run_guess", "df_mlp_create",
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
-            "df_fp64_rate", "df_sad_density", "df_build_B_batch"]
+            "df_fp64_rate", "df_sad_density", "df_build_B_batch",
+            "df_init_open", "scf_run_uhf"]
 DF_MLP_NFEAT = 57
 
 
@@ -49,7 +50,7 @@ class Result(ctypes.Structure):
                 ("status", ctypes.c_int), ("n_dropped", ctypes.c_int), ("ramp_iteration", ctypes.c_int),
                 ("incremental_builds", ctypes.c_int), ("approx_steps", ctypes.c_int), ("t_build_s", ctypes.c_double),
                 ("t_iter_s", ctypes.c_double), ("t_jk_s", ctypes.c_double), ("t_total_s", ctypes.c_double),
-                ("graph_launches", ctypes.c_int)]
+                ("s2", ctypes.c_double), ("graph_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -87,6 +88,8 @@ def load(path: str | None = None):
     L.df_fp64_rate.argtypes = [c_int, ctypes.c_longlong, dp, dp]
     L.df_sad_density.argtypes = [c_void_p, dp]
     L.df_build_B_batch.argtypes = [P(c_void_p), c_int, c_double, c_int, c_int]
+    L.df_init_open.argtypes = [P(Atom), c_int, P(Shell), c_int, P(Shell), c_int, c_int, P(c_void_p)]
+    L.scf_run_uhf.argtypes = [c_void_p, P(Options), c_int, c_int, P(Result)]
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
@@ -145,19 +148,22 @@ def _atoms(arr):
     return out
 
 
-MATRIX = {"S": 0, "T": 1, "V": 2, "H": 3, "metric": 4, "Linv": 5, "D": 6, "F": 7, "J": 8, "K": 9, "C": 10, "eps": 11}
+MATRIX = {"S": 0, "T": 1, "V": 2, "H": 3, "metric": 4, "Linv": 5, "D": 6, "F": 7, "J": 8, "K": 9, "C": 10, "eps": 11,
+          "Da": 12, "Db": 13}
 
 
 class Handle:
     """One molecule on the GPU: wraps df_init ... df_free."""
 
-    def __init__(self, system):
+    def __init__(self, system, open_shell: bool = False):
+        """open_shell: df_init_open (any electron count, for scf_uhf)."""
         L = load()
         self.system = system
         h = ctypes.c_void_p()
         atoms, basis, aux = _atoms(system.atoms), _shells(system.basis), _shells(system.aux)
-        rc = L.df_init(atoms, len(system.atoms), basis, len(system.basis), aux, len(system.aux), int(system.charge),
-                       ctypes.byref(h))
+        init = L.df_init_open if open_shell else L.df_init
+        rc = init(atoms, len(system.atoms), basis, len(system.basis), aux, len(system.aux), int(system.charge),
+                  ctypes.byref(h))
         if rc != DF_OK:
             raise DFError(rc, "df_init")
         self.h = h
@@ -233,6 +239,16 @@ class Handle:
         D0 = np.empty((self.n, self.n))
         self._check(load().df_mlp_guess(self.h, mlp.m, int(bf16), _dp(D0)), "df_mlp_guess")
         return D0
+
+    def scf_uhf(self, nalpha, nbeta, conv_E=1e-10, conv_err=1e-7, max_iter=200, diis_size=8, precision=DF_PREC_FP64,
+                slices=3, screen_tau=0.0):
+        """Unrestricted Hartree-Fock (scf_run_uhf) with nalpha and nbeta electrons."""
+        o = Options(conv_E, conv_err, max_iter, diis_size, DF_GUESS_CORE, precision, slices, 0, screen_tau, 0)
+        r = Result()
+        rc = load().scf_run_uhf(self.h, ctypes.byref(o), int(nalpha), int(nbeta), ctypes.byref(r))
+        if rc not in (DF_OK, DF_E_NOTCONV):
+            self._check(rc, "scf_run_uhf")
+        return r.as_dict()
 
     def sad_density(self):
         """The superposition-of-atomic-densities guess density (n x n), df_sad_density."""

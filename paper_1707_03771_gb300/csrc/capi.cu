@@ -584,6 +584,7 @@ int df_jk(df_handle* h, const double* D, const double* C_occ, int nocc, double* 
 
 int scf_run(df_handle* h, const df_options* opts, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
+    if (h->nelec % 2) return fail(h, Error{DF_E_STATE, "restricted Hartree-Fock needs an even electron count (scf_run_uhf)"});
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
         (opts->approx_diag != 0 && opts->approx_diag != 1) ||
         (opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SAD)) return DF_E_ARG;
@@ -600,6 +601,7 @@ int scf_run(df_handle* h, const df_options* opts, df_result* out) {
 
 int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_result* out) {
     if (!h || !opts || !out) return DF_E_ARG;
+    if (h->nelec % 2) return fail(h, Error{DF_E_STATE, "restricted Hartree-Fock needs an even electron count (scf_run_uhf)"});
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0 ||
         (opts->approx_diag != 0 && opts->approx_diag != 1) ||
         (opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SAD)) return DF_E_ARG;
@@ -624,6 +626,7 @@ int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* o
     int dev = -1;
     for (int i = 0; i < nmol; ++i) {
         if (!hs[i]) return DF_E_ARG;
+        if (hs[i]->nelec % 2) return DF_E_STATE;   // restricted Hartree-Fock: even electron counts only
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return DF_E_ARG;   // each molecule needs its own handle
         if (dev < 0) dev = hs[i]->device;
@@ -638,6 +641,29 @@ int scf_run_batch(df_handle** hs, int nmol, const df_options* opts, df_result* o
             if (out[i].status == 0 && !out[i].converged) out[i].status = e.code;
         }
         return e.code;
+    }
+}
+
+int df_init_open(const df_atom* atoms, int natom, const df_shell* basis, int nbasis_sh, const df_shell* aux,
+                 int naux_sh, int charge, df_handle** out) {
+    return dfhf::init_handle(atoms, natom, basis, nbasis_sh, aux, naux_sh, charge, out, false);
+}
+
+int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_result* out) {
+    if (!h || !opts || !out) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
+    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
+    if (opts->guess != DF_GUESS_CORE || opts->incremental || opts->approx_diag)
+        return fail(h, Error{DF_E_ARG, "scf_run_uhf: core-Hamiltonian guess, full builds and full eigensolves only"});
+    if (nalpha < nbeta || nbeta < 0 || nalpha + nbeta != h->nelec || nalpha > h->n)
+        return fail(h, Error{DF_E_ARG, "scf_run_uhf: need nalpha >= nbeta >= 0, nalpha + nbeta = electron count"});
+    try {
+        DF_CUDA(cudaSetDevice(h->device));
+        return scf_drive_uhf(h, opts, nalpha, nbeta, out);
+    } catch (const Error& e) {
+        out->status = e.code;
+        return fail(h, e);
     }
 }
 
@@ -677,6 +703,8 @@ int df_get_matrix(df_handle* h, int which, double* out) {
         case 9: src = h->dK.p; break;
         case 10: src = h->C.p; count = (size_t)h->n * h->nX; break;
         case 11: src = h->eps.p; count = h->n; break;
+        case 12: src = h->Dspin.p; break;                             // UHF alpha density
+        case 13: src = h->Dspin.p ? h->Dspin.p + nn : nullptr; break;   // UHF beta density
         default: return DF_E_ARG;
     }
     if (!src) return fail(h, Error{DF_E_STATE, "matrix not available yet"});
@@ -767,7 +795,7 @@ void df_free(df_handle* h) {
     DevBuf<double>* bufs[] = {&h->d_atom_xyz, &h->d_atom_Z, &h->S, &h->T, &h->V, &h->H, &h->metric, &h->Linv,
                               &h->A3c, &h->B, &h->Dw, &h->gamma, &h->Jp, &h->Y, &h->Kpart, &h->Cpad, &h->dD,
                               &h->dC, &h->dJ, &h->dK, &h->X, &h->F, &h->Fx, &h->Dm, &h->C, &h->eps, &h->work1,
-                              &h->work2, &h->work3, &h->diisF, &h->diisE, &h->diisB};
+                              &h->work2, &h->work3, &h->diisF, &h->diisE, &h->diisB, &h->Dspin};
     for (auto* b : bufs) b->release();
     h->ktiles.release();
     for (auto& b : h->d_aux_by_l) b.release();

@@ -160,6 +160,7 @@ struct df_handle {
 
     // SCF state
     dfhf::DevBuf<double> X, F, Fx, Dm, C, eps, work1, work2, work3, diisF, diisE, diisB;
+    dfhf::DevBuf<double> Dspin;   // alpha | beta densities of the last UHF run
     int nX = 0;
     int ndrop = 0;
 
@@ -223,6 +224,7 @@ std::vector<double> aufbau_occupations(const std::vector<double>& eps, double ne
 // superposition of atomic densities (sad.cu): C0 (device, n x m0) with D0 = 2 C0 C0^T
 void sad_factor(df_handle* h, DevBuf<double>& C0, int& m0);
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
+int scf_drive_uhf(df_handle* h, const df_options* o, int nalpha, int nbeta, df_result* r);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
 

@@ -279,6 +279,21 @@ __global__ void invsqrt_series_kernel(double* __restrict__ M, const double* __re
     M[idx] = (idx / m == idx % m ? 1.875 : 0.0) - 1.25 * M[idx] + 0.375 * M2[idx];
 }
 
+// c = a + b
+__global__ void add_kernel2(const double* __restrict__ a, const double* __restrict__ b, long long len,
+                            double* __restrict__ c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) c[i] = a[i] + b[i];
+}
+
+// T = A^T (n x n)
+__global__ void transpose_kernel(const double* __restrict__ A, int n, double* __restrict__ T) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    T[idx] = A[(long long)j * n + i];
+}
+
 // a += b
 __global__ void add_inplace_kernel(double* __restrict__ a, const double* __restrict__ b, long long len) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -981,6 +996,285 @@ class ScfRun {
     bool saved_sync_timing_ = true;
 };
 
+// Unrestricted Hartree-Fock (paper, section "Program features", "Standard algorithms": UHF on the
+// density-fitted Fock builder). Spin densities D_s = C_s C_s^T (no factor 2); J from D_a + D_b (eq. 3);
+// K_s = sum_{P,i in s} Y Y^T from the spin's occupied orbitals (eqs. 1-2, first forms; FP64 or split
+// precision, the split form at 3 slices until max|e| < 1e-4 and 5 slices after, converging only on the
+// 5-slice builds); F_s = H + J - K_s; E = 1/2 tr(D_a (H + F_a)) + 1/2 tr(D_b (H + F_b)) + E_nuc. Pulay DIIS
+// over the stacked pair (F'_a, F'_b) with errors F'_s P_s - P_s F'_s (P_s = V_s,occ V_s,occ^T; the
+// orthogonal-basis form of X^T (F_s D_s S - S D_s F_s) X), one set of coefficients for both spins;
+// core-Hamiltonian start for both spins; every step on the device in FP64 except the exchange contraction.
+class UhfRun {
+  public:
+    UhfRun(df_handle* h, const df_options* o, int na, int nb, df_result* r) : h_(h), o_(*o), r_(r), na_(na), nb_(nb) {}
+    ~UhfRun() { release(); }
+
+    int run() {
+        const auto t_start = std::chrono::steady_clock::now();
+        *r_ = df_result{};
+        r_->e_nuc = h_->e_nuc;
+        if (!h_->built) {
+            const auto t0 = std::chrono::steady_clock::now();
+            build_B(h_, o_.screen_tau, false, o_.precision == DF_PREC_FP64 ? DF_WHITEN_FP64 : DF_WHITEN_SPLIT);
+            r_->t_build_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        n_ = h_->n;
+        nn_ = (long long)n_ * n_;
+        s_ = h_->stream;
+        slices_ = o_.slices;
+        const int dsize = std::max(2, std::min(o_.diis_size, DIIS_MAX));
+        DF_CUDA(cudaMalloc((void**)&info_, sizeof(int)));
+        DF_CUDA(cudaHostAlloc((void**)&pin_, sizeof(double) * 8, cudaHostAllocDefault));
+        h_->work1.alloc(nn_);
+        h_->work2.alloc(nn_);
+        h_->work3.alloc(nn_);
+        h_->eps.alloc(2 * (size_t)n_);
+        // canonical orthogonaliser X = U s^{-1/2} (eigenvalues of S below 1e-7 dropped)
+        DF_CUDA(cudaMemcpyAsync(h_->work1.p, h_->S.p, nn_ * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+        eig(h_->work1.p, n_, h_->eps.p);
+        std::vector<double> sv(n_);
+        int hinfo = 0;
+        DF_CUDA(cudaMemcpyAsync(sv.data(), h_->eps.p, n_ * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaMemcpyAsync(&hinfo, info_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaStreamSynchronize(s_));
+        if (hinfo != 0) throw Error{DF_E_NUMERIC, "dsyevd of S failed, info " + std::to_string(hinfo)};
+        int first = 0;
+        while (first < n_ && sv[first] <= 1e-7) ++first;
+        nX_ = n_ - first;
+        if (nX_ < na_) throw Error{DF_E_NUMERIC, "orthogonal basis smaller than the alpha occupied space"};
+        r_->n_dropped = first;
+        h_->X.alloc((size_t)n_ * nX_);
+        build_x_kernel<<<nblk((long long)n_ * nX_), 256, 0, s_>>>(h_->work1.p, h_->eps.p, n_, first, nX_, h_->X.p);
+        DF_CHECK_LAUNCH();
+        const long long no = (long long)nX_ * nX_;
+        ensure_jk_buffers(h_, std::max(na_, 1));
+        auto dalloc = [](double** p, long long count) { DF_CUDA(cudaMalloc((void**)p, sizeof(double) * count)); };
+        dalloc(&D_, 3 * nn_);               // D_a | D_b | D_a + D_b
+        dalloc(&F_, 2 * nn_);               // F_a | F_b
+        dalloc(&Kb_, nn_);
+        dalloc(&C_, (long long)n_ * (na_ + std::max(nb_, 1)));   // C_a (n x na) | C_b (n x nb)
+        dalloc(&Fo_, 2 * no);               // F'_a | F'_b
+        dalloc(&V_, 2 * no);                // eigenvectors (rows) of the alpha and beta Roothaan steps
+        dalloc(&T1_, (long long)n_ * nX_);
+        dalloc(&diisF_, DIIS_MAX * 2 * no);
+        dalloc(&diisE_, DIIS_MAX * 2 * no);
+        dalloc(&Bm_, DIIS_MAX * DIIS_MAX + 8 + DIIS_MAX);   // B matrix | scalars | coefficients
+        DF_CUDA(cudaMalloc((void**)&ints_, sizeof(int) * (2 * DIIS_MAX + 4)));
+        DF_CUDA(cudaMemsetAsync(ints_, 0, sizeof(int) * (2 * DIIS_MAX + 4), s_));
+        double* scal = Bm_ + DIIS_MAX * DIIS_MAX;
+        double* coef = scal + 8;
+        int* slotp = ints_ + 2 * DIIS_MAX + 3;
+        std::vector<int> present(DIIS_MAX, 0), order;
+        std::vector<int> ctl(2 * DIIS_MAX + 4, 0);
+        // core-Hamiltonian start for both spins
+        to_orth(h_->H.p, Fo_);
+        DF_CUDA(cudaMemcpyAsync(Fo_ + no, Fo_, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+        roothaan(Fo_);
+        const auto t_iter = std::chrono::steady_clock::now();
+        double e_old = 0.0, jk_ms = 0.0;
+        int status = DF_E_NOTCONV;
+        cudaEvent_t j0, j1;
+        DF_CUDA(cudaEventCreate(&j0));
+        DF_CUDA(cudaEventCreate(&j1));
+        h_->history.clear();
+        for (int it = 1; it <= o_.max_iter; ++it) {
+            DF_CUDA(cudaEventRecord(j0, s_));
+            coulomb_fp64(h_, D_ + 2 * nn_, h_->dJ.p);
+            exchange_only(h_, C_, na_, o_.precision, slices_, h_->dK.p);
+            if (nb_ > 0) exchange_only(h_, C_ + (long long)n_ * na_, nb_, o_.precision, slices_, Kb_);
+            else DF_CUDA(cudaMemsetAsync(Kb_, 0, sizeof(double) * nn_, s_));
+            DF_CUDA(cudaEventRecord(j1, s_));
+            fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, h_->dK.p, nn_, F_);
+            DF_CHECK_LAUNCH();
+            fock_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->H.p, h_->dJ.p, Kb_, nn_, F_ + nn_);
+            DF_CHECK_LAUNCH();
+            energy_kernel<<<1, 1024, 0, s_>>>(D_, h_->H.p, h_->dJ.p, h_->dK.p, nn_, scal);
+            DF_CHECK_LAUNCH();
+            energy_kernel<<<1, 1024, 0, s_>>>(D_ + nn_, h_->H.p, h_->dJ.p, Kb_, nn_, scal + 4);
+            DF_CHECK_LAUNCH();
+            // DIIS slot of this iteration
+            int slot = 0;
+            if ((int)order.size() < dsize) {
+                while (present[slot]) ++slot;
+            } else {
+                slot = order.front();
+                order.erase(order.begin());
+                present[slot] = 0;
+            }
+            double* E = diisE_ + (long long)slot * 2 * no;
+            for (int sp = 0; sp < 2; ++sp) {
+                const int nocc = sp == 0 ? na_ : nb_;
+                double* Fos = Fo_ + sp * no;
+                to_orth(F_ + sp * nn_, Fos);
+                if (nocc > 0) {
+                    const double* Vo = V_ + sp * no;   // occupied rows first
+                    dgemm(s_, false, true, nX_, nocc, nX_, 1.0, Fos, nX_, Vo, nX_, 0.0, h_->work2.p, nocc);
+                    dgemm(s_, false, false, nX_, nX_, nocc, 1.0, h_->work2.p, nocc, Vo, nX_, 0.0, h_->work1.p, nX_);
+                    antisym_kernel<<<nblk(no), 256, 0, s_>>>(h_->work1.p, nX_, 1.0, E + sp * no);
+                    DF_CHECK_LAUNCH();
+                } else {
+                    DF_CUDA(cudaMemsetAsync(E + sp * no, 0, sizeof(double) * no, s_));
+                }
+            }
+            absmax_kernel<<<1, 1024, 0, s_>>>(E, 2 * no, scal + 3);
+            DF_CHECK_LAUNCH();
+            DF_CUDA(cudaMemcpyAsync(pin_, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+            DF_CUDA(cudaStreamSynchronize(s_));
+            const double this_jk = elapsed_ms(j0, j1);
+            jk_ms += this_jk;
+            const double energy = pin_[0] + 0.5 * pin_[1] - 0.5 * pin_[2] + pin_[4] + 0.5 * pin_[5] - 0.5 * pin_[6] +
+                                  h_->e_nuc;
+            const double err = pin_[3];
+            h_->history.insert(h_->history.end(), {(double)it, energy, it > 1 ? energy - e_old : 0.0, err,
+                                                   o_.precision == DF_PREC_SPLIT ? (double)slices_ : 0.0, this_jk});
+            r_->iterations = it;
+            r_->energy = energy;
+            r_->e_one = pin_[0] + pin_[4];
+            r_->e_coul = 0.5 * (pin_[1] + pin_[5]);
+            r_->e_exch = -0.5 * (pin_[2] + pin_[6]);
+            r_->last_err = err;
+            r_->last_dE = it > 1 ? energy - e_old : 0.0;
+            if (!std::isfinite(energy) || !std::isfinite(err)) {
+                status = DF_E_NUMERIC;
+                break;
+            }
+            const bool late_ready = o_.precision != DF_PREC_SPLIT || slices_ >= SPLIT_LATE_SLICES;
+            if (it > 1 && late_ready && std::fabs(energy - e_old) < o_.conv_E && err < o_.conv_err) {
+                status = DF_OK;
+                break;
+            }
+            e_old = energy;
+            if (o_.precision == DF_PREC_SPLIT && slices_ < SPLIT_LATE_SLICES && err < SPLIT_RAMP_ERR) {
+                slices_ = SPLIT_LATE_SLICES;   // the DIIS subspace restarts with the finer exchange
+                r_->ramp_iteration = it + 1;
+                for (int q : order) present[q] = 0;
+                order.clear();
+            }
+            DF_CUDA(cudaMemcpyAsync(diisF_ + (long long)slot * 2 * no, Fo_, sizeof(double) * 2 * no,
+                                    cudaMemcpyDeviceToDevice, s_));
+            present[slot] = 1;
+            order.push_back(slot);
+            for (int q = 0; q < DIIS_MAX; ++q) ctl[q] = present[q];
+            for (size_t q = 0; q < order.size(); ++q) ctl[DIIS_MAX + q] = order[q];
+            ctl[2 * DIIS_MAX + 3] = slot;
+            DF_CUDA(cudaMemcpyAsync(ints_, ctl.data(), sizeof(int) * (2 * DIIS_MAX + 4), cudaMemcpyHostToDevice, s_));
+            diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(diisE_, 2 * no, slotp, ints_, DIIS_MAX, Bm_);
+            DF_CHECK_LAUNCH();
+            if (it >= 2 && order.size() >= 2) {
+                diis_solve_kernel<<<1, 1, 0, s_>>>(Bm_, ints_ + DIIS_MAX, (int)order.size(), coef, ints_ + 2 * DIIS_MAX);
+                DF_CHECK_LAUNCH();
+                diis_combine_kernel<<<nblk(2 * no), 256, 0, s_>>>(diisF_, 2 * no, ints_ + DIIS_MAX, (int)order.size(),
+                                                                 coef, Fo_);
+                DF_CHECK_LAUNCH();
+                int singular = 0;
+                DF_CUDA(cudaMemcpyAsync(&singular, ints_ + 2 * DIIS_MAX, sizeof(int), cudaMemcpyDeviceToHost, s_));
+                DF_CUDA(cudaStreamSynchronize(s_));   // ctl (host) is rewritten next iteration
+                if (singular && order.size() > 1) {   // drop the oldest vector from the subspace
+                    present[order.front()] = 0;
+                    order.erase(order.begin());
+                }
+            } else {
+                DF_CUDA(cudaStreamSynchronize(s_));   // ctl (host) is rewritten next iteration
+            }
+            roothaan(Fo_);
+        }
+        cudaEventDestroy(j0);
+        cudaEventDestroy(j1);
+        r_->s2 = spin_s2();
+        r_->converged = status == DF_OK;
+        r_->status = status;
+        r_->t_iter_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_iter).count();
+        r_->t_jk_s = jk_ms / 1000.0;
+        r_->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        // the total density becomes the handle's D (df_get_matrix), the spin densities its spin buffers
+        if (!h_->Dm.p) h_->Dm.alloc(nn_);
+        h_->Dspin.alloc(2 * nn_);
+        DF_CUDA(cudaMemcpyAsync(h_->Dm.p, D_ + 2 * nn_, sizeof(double) * nn_, cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaMemcpyAsync(h_->Dspin.p, D_, sizeof(double) * 2 * nn_, cudaMemcpyDeviceToDevice, s_));
+        DF_CUDA(cudaStreamSynchronize(s_));
+        return status;
+    }
+
+  private:
+    // Roothaan step for both spins from F'_a | F'_b held in Fs (overwritten by the eigenvectors)
+    void roothaan(double* Fs) {
+        const long long no = (long long)nX_ * nX_;
+        for (int sp = 0; sp < 2; ++sp) {
+            const int nocc = sp == 0 ? na_ : nb_;
+            DF_CUDA(cudaMemcpyAsync(V_ + sp * no, Fs + sp * no, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+            eig(V_ + sp * no, nX_, h_->eps.p + sp * n_);
+            double* C = C_ + (sp == 0 ? 0 : (long long)n_ * na_);
+            double* D = D_ + sp * nn_;
+            if (nocc > 0) {
+                dgemm(s_, false, true, n_, nocc, nX_, 1.0, h_->X.p, nX_, V_ + sp * no, nX_, 0.0, C, nocc);
+                dgemm(s_, false, true, n_, n_, nocc, 1.0, C, nocc, C, nocc, 0.0, D, n_);
+            } else {
+                DF_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * nn_, s_));
+            }
+        }
+        add_kernel2<<<nblk(nn_), 256, 0, s_>>>(D_, D_ + nn_, nn_, D_ + 2 * nn_);
+        DF_CHECK_LAUNCH();
+    }
+
+    // <S^2> = S_z (S_z + 1) + n_beta - tr(D_a S D_b S)
+    double spin_s2() {
+        dgemm(s_, false, false, n_, n_, n_, 1.0, D_, n_, h_->S.p, n_, 0.0, h_->work1.p, n_);          // D_a S
+        dgemm(s_, false, false, n_, n_, n_, 1.0, D_ + nn_, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);    // D_b S
+        transpose_kernel<<<nblk(nn_), 256, 0, s_>>>(h_->work2.p, n_, h_->work3.p);
+        double* scal = Bm_ + DIIS_MAX * DIIS_MAX;
+        energy_kernel<<<1, 1024, 0, s_>>>(h_->work1.p, h_->work3.p, h_->work3.p, h_->work3.p, nn_, scal);
+        DF_CHECK_LAUNCH();
+        double tr = 0.0;
+        DF_CUDA(cudaMemcpyAsync(&tr, scal, sizeof(double), cudaMemcpyDeviceToHost, s_));
+        DF_CUDA(cudaStreamSynchronize(s_));
+        const double sz = 0.5 * (na_ - nb_);
+        return sz * (sz + 1.0) + nb_ - tr;
+    }
+
+    void eig(double* A, int m, double* w) {
+        int lw = 0;
+        DF_SOLVER(cusolverDnDsyevd_bufferSize(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, &lw));
+        if (lw > lwork_) {
+            if (work_) cudaFree(work_);
+            work_ = nullptr;
+            DF_CUDA(cudaMalloc((void**)&work_, sizeof(double) * lw));
+            lwork_ = lw;
+        }
+        DF_SOLVER(cusolverDnDsyevd(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m, w, work_,
+                                   lwork_, info_));
+    }
+
+    // Fo = X^T Fm X (nX x nX)
+    void to_orth(const double* Fm, double* Fo) {
+        dgemm(s_, false, false, n_, nX_, n_, 1.0, Fm, n_, h_->X.p, nX_, 0.0, T1_, nX_);
+        dgemm(s_, true, false, nX_, nX_, n_, 1.0, h_->X.p, nX_, T1_, nX_, 0.0, Fo, nX_);
+    }
+
+    void release() {
+        if (s_) cudaStreamSynchronize(s_);
+        double* bufs[] = {D_, F_, Kb_, C_, Fo_, V_, T1_, diisF_, diisE_, Bm_, work_};
+        for (double* b : bufs)
+            if (b) cudaFree(b);
+        if (ints_) cudaFree(ints_);
+        if (info_) cudaFree(info_);
+        if (pin_) cudaFreeHost(pin_);
+        D_ = F_ = Kb_ = C_ = Fo_ = V_ = T1_ = diisF_ = diisE_ = Bm_ = work_ = nullptr;
+        ints_ = info_ = nullptr;
+        pin_ = nullptr;
+    }
+
+    df_handle* h_;
+    df_options o_;
+    df_result* r_;
+    int na_, nb_;
+    int n_ = 0, nX_ = 0, slices_ = 3, lwork_ = 0;
+    long long nn_ = 0;
+    cudaStream_t s_ = nullptr;
+    double *D_ = nullptr, *F_ = nullptr, *Kb_ = nullptr, *C_ = nullptr, *Fo_ = nullptr, *V_ = nullptr, *T1_ = nullptr;
+    double *diisF_ = nullptr, *diisE_ = nullptr, *Bm_ = nullptr, *work_ = nullptr, *pin_ = nullptr;
+    int *ints_ = nullptr, *info_ = nullptr;
+};
+
 }  // namespace
 
 // Fractional-occupation SCF of one atom (handle ha, nelec electrons), FP64, converged to |dE| < 1e-11 and
@@ -1010,6 +1304,11 @@ void atomic_scf(df_handle* ha, double nelec, std::vector<double>& Cw, int& m) {
     Cw.resize((size_t)ha->n * m);
     DF_CUDA(cudaStreamSynchronize(ha->stream));
     DF_CUDA(cudaMemcpy(Cw.data(), run.occupied_factor(), sizeof(double) * Cw.size(), cudaMemcpyDeviceToHost));
+}
+
+int scf_drive_uhf(df_handle* h, const df_options* o, int nalpha, int nbeta, df_result* r) {
+    UhfRun run(h, o, nalpha, nbeta, r);
+    return run.run();
 }
 
 int scf_drive(df_handle* h, const df_options* o, df_result* r, const double* guess) {
