@@ -395,9 +395,10 @@ __global__ void __launch_bounds__(256) split_y_kernel(const float2* __restrict__
         }
 }
 
-// Y (hi, lo) -> Ys[s][mu][k] over the contiguous contraction index k = P ldy + i (KL = naux ldy values per
-// row mu), one exponent per (mu, chunk of CH consecutive k): the operand layout of the tensor-core exchange
-// contraction (no padding between auxiliary rows); warp per (mu, chunk)
+// Y (hi, lo) -> Ys over the contiguous contraction index k = P ldy + i (KL = naux ldy values per row mu), one
+// exponent per (mu, chunk of CH consecutive k): the operand layout of the tensor-core exchange contraction.
+// Tile-major: Ys[s][k / 64][mu][k % 64], so that one TMA box (128 rows x 64 k) is 16 KB of contiguous memory;
+// no padding between auxiliary rows; the tail of the last 64-block (k >= KL) is zero. Warp per (mu, chunk).
 template <int S>
 __global__ void __launch_bounds__(256) split_y_rows_kernel(const float2* __restrict__ Y, int np, int ldy, long long KL,
                                                            int CH, bf16* __restrict__ Ys, int* __restrict__ Ye) {
@@ -408,30 +409,60 @@ __global__ void __launch_bounds__(256) split_y_rows_kernel(const float2* __restr
     const int mu = (int)(warp % np);
     const long long b = warp / np;
     const long long k0 = b * CH, k1 = min(KL, k0 + CH);
-    auto at = [&](long long k) { return Y[((k / ldy) * np + mu) * ldy + k % ldy]; };
+    const long long nkb = (KL + 63) / 64;
+    const long long sstride = nkb * np * 64;
+    // the chunk's k run over auxiliary rows P0, P0 + 1, ...: one division per warp, then per-row segments
+    const long long P0 = k0 / ldy;
+    const int i0 = (int)(k0 - P0 * ldy);
     float mx = 0.f;
-    for (long long k = k0 + lane; k < k1; k += 32) mx = fmaxf(mx, fabsf(at(k).x));
+    {
+        long long k = k0, P = P0;
+        int i = i0;
+        while (k < k1) {
+            const int seg = (int)min((long long)(ldy - i), k1 - k);
+            const float2* y = Y + (P * np + mu) * ldy + i;
+            for (int j = lane; j < seg; j += 32) mx = fmaxf(mx, fabsf(y[j].x));
+            k += seg;
+            ++P;
+            i = 0;
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);   // |hi + lo| 2^-e <= 1 + 2^-24, so |m_1| <= 128 still holds
     if (lane == 0) Ye[b * np + mu] = e;
     const float sc = pow2f(-e);
-    const long long sstride = (long long)np * KL;
-    for (long long k = k0 + lane; k < k1; k += 32) {
-        const float2 y = at(k);
-        float r = y.x * sc;
-        float rl = y.y * sc;
-        bf16* out = Ys + (long long)mu * KL + k;
+    long long k = k0, P = P0;
+    int i = i0;
+    while (k < k1) {
+        const int seg = (int)min((long long)(ldy - i), k1 - k);
+        const float2* y = Y + (P * np + mu) * ldy + i;
+        for (int j = lane; j < seg; j += 32) {
+            const float2 v = y[j];
+            const long long kk = k + j;
+            bf16* out = Ys + ((kk >> 6) * np + mu) * 64 + (kk & 63);
+            float r = v.x * sc;
+            float rl = v.y * sc;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const float tt = r * 128.f;
-            const float m = rintf(tt);
-            r = (tt - m) + rl * 128.f;
-            rl = 0.f;
-            out[s * sstride] = __float2bfloat16_rn(m);
+            for (int s = 0; s < S; ++s) {
+                const float tt = r * 128.f;
+                const float m = rintf(tt);
+                r = (tt - m) + rl * 128.f;
+                rl = 0.f;
+                out[s * sstride] = __float2bfloat16_rn(m);
+            }
         }
+        k += seg;
+        ++P;
+        i = 0;
     }
+    if (k1 == KL)   // the warps of the last chunk zero the tail of the last 64-block
+        for (long long kk = KL + lane; kk < nkb * 64; kk += 32) {
+            bf16* out = Ys + ((kk >> 6) * np + mu) * 64 + (kk & 63);
+#pragma unroll
+            for (int s = 0; s < S; ++s) out[s * sstride] = __float2bfloat16_rn(0.f);
+        }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -759,7 +790,8 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
         h->exchange_launches = 4 + nyb * (st->blocked ? 2 : 1);
     }
     const long long ystr = (long long)naux * np * ldy;
-    // the tensor-core contraction takes Ys[s][mu][k] (k = P ldy + i, chunks of the exact length for S); the
+    // the tensor-core contraction takes Ys[s][k / 64][mu][k % 64] (k = P ldy + i, chunks of the exact length
+    // for S); the
     // mma.sync contraction Ys[s][P][mu][i] with chunks of PB auxiliary rows
     const long long nblk = tc ? ((long long)naux * ldy + exact_chunk<S>() - 1) / exact_chunk<S>()
                               : (naux + st->PB - 1) / st->PB;
@@ -904,7 +936,8 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
             DF_CUDA(cudaMalloc((void**)&st->Cs, sizeof(bf16) * st->S * (long long)ldy * np));
             DF_CUDA(cudaMalloc((void**)&st->Ce, sizeof(int) * ldy));
             DF_CUDA(cudaMalloc((void**)&st->Y, sizeof(float2) * (long long)h->naux * np * ldy));
-            DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * (long long)h->naux * np * ldy));
+            // (P, mu, i) slices for the mma.sync contraction, or (k block, mu, 64) with the last block padded
+            DF_CUDA(cudaMalloc((void**)&st->Ys, sizeof(bf16) * st->S * np * ((long long)h->naux * ldy + 64)));
             st->ldy_cap = ldy;
         }
         // exponents per block: PB auxiliary rows (mma.sync layout) or an exact chunk of the contiguous

@@ -151,14 +151,15 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 // Work description. MODE 0 (Y = B C): CTA = (P, mu-tile, n-tile); K runs over nu (np), exponents
 // constant (row: Be[P][mu], column: Ce[i]). MODE 1 (K = sum Y Y^T): CTA = (split, lower tile pair,
 // column part), the split slowest so that the CTAs resident together stream the same range of the
-// contraction through L2; K runs over the contiguous index k = P ldy + i of the Y slices Ys[s][mu][k]
-// (no padding between auxiliary rows), one exact chunk per block of `chunk` consecutive k with its own
-// exponents Ye[block][mu], Ye[block][nu].
+// contraction through L2; K runs over the contiguous index k = P ldy + i of the Y slices, stored tile-major
+// as Ys[s][k / 64][mu][k % 64] (one TMA box is 16 KB of contiguous memory; no padding between auxiliary
+// rows), one exact chunk per block of consecutive k with its own exponents Ye[block][mu], Ye[block][nu].
 // ------------------------------------------------------------------------------------------------
 struct TcArgs {
     int mode;
     int naux, np, ldy, PB, nsplit;
     long long KL;            // MODE 1: naux * ldy, the length of the contraction
+    int nkb;                 // MODE 1: 64-wide blocks of the contraction, ceil(KL / 64)
     int ntiles;              // MODE 1: lower 128-tile pairs
     const int* row_e;        // MODE 0: Be [naux][np]; MODE 1: Ye [nchunk][np]
     const int* col_e;        // MODE 0: Ce [ldy]
@@ -276,12 +277,16 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
             asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&mapB) : "memory");
             int a_issued = 0, b_issued = 0;
             for (int ks = 0; ks < ksteps; ++ks) {
-                // x: the contraction coordinate of this K-step (MODE 1: from the split's first K-step)
-                const int kx = MODE == 1 ? (kpp + ks) * KS : ks * KS;
+                // x: the contraction coordinate of this K-step; MODE 1 reads the tile-major slices
+                // [s][k block][row][64] at x = 0 and z = s nkb + the split's K-step
+                const int kx = MODE == 1 ? 0 : ks * KS;
+                const int kb = kpp + ks;
                 const int bs = ks & 1;
                 if (!mbar_wait(&b_empty[bs], ((ks >> 1) & 1) ^ 1, err, wait)) break;
                 mbar_expect_tx(&b_full[bs], BSET);
-                for (int t = 0; t < S; ++t) tma_load_3d(bbuf + bs * BSET + t * B_BYTES, &mapB, kx, n0, t, &b_full[bs]);
+                for (int t = 0; t < S; ++t)
+                    tma_load_3d(bbuf + bs * BSET + t * B_BYTES, &mapB, kx, n0, MODE == 1 ? t * args.nkb + kb : t,
+                                &b_full[bs]);
                 ++b_issued;
                 bool ok = true;
                 for (int s = 0; s < S; ++s) {
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                         break;
                     }
                     mbar_expect_tx(&a_full[slot], A_BYTES);
-                    const int za = MODE == 0 ? s * args.naux + P : s;
+                    const int za = MODE == 0 ? s * args.naux + P : (MODE == 1 ? s * args.nkb + kb : s);
                     tma_load_3d(smem + slot * A_BYTES, &mapA, kx, m0, za, &a_full[slot]);
                     ++a_issued;
                 }
@@ -588,7 +593,8 @@ void whiten_tc(cudaStream_t s, int N, const bf16* Ls, const int* eL, const bf16*
 }
 
 // K partial sums over lower 128-tile pairs: Kpart [nsplit][npt][npt] (float pairs), from the Y slices
-// Ys [S][np][KL] (KL = naux ldy, contraction index k = P ldy + i contiguous) with exponents Ye [chunk][np]
+// Ys [S][KL / 64][np][64] (KL = naux ldy over the contraction index k = P ldy + i, tile-major) with exponents
+// Ye [chunk][np]
 template <int N>
 void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int nsplit,
                   const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err) {
@@ -598,6 +604,7 @@ void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux
     a.np = np;
     a.ldy = ldy;
     a.KL = (long long)naux * ldy;
+    a.nkb = (int)((a.KL + KS - 1) / KS);
     a.ntiles = ntiles;
     a.nsplit = nsplit;
     a.row_e = Ye;
@@ -605,8 +612,8 @@ void k_split_tc_n(cudaStream_t s, int S, const bf16* Ys, const int* Ye, int naux
     a.out = Kpart;
     a.npt = npt;
     a.err = err;
-    const CUtensorMap ma = make_map(Ys, (unsigned long long)a.KL, np, S, TM);
-    const CUtensorMap mb = make_map(Ys, (unsigned long long)a.KL, np, S, N);
+    const CUtensorMap ma = make_map(Ys, KS, np, (unsigned long long)S * a.nkb, TM);
+    const CUtensorMap mb = make_map(Ys, KS, np, (unsigned long long)S * a.nkb, N);
     const unsigned grid = (unsigned)ntiles * nsplit * (TM / N);
     switch (S) {
         case 3: launch_tc<3, N, 1>(s, ma, mb, a, grid); break;
