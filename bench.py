@@ -498,17 +498,21 @@ def c2_measure(args, binding, clusters, lib, dev, stream, guess_net):
 def train_guess(binding, clusters, members, epochs=200, precision=None):
     """Train the density-guess network on the converged densities of the seeded clusters `members`
     ((waters, seed) pairs), generated by this library's SCF. Returns (network, summary)."""
+    import torch
     t0 = time.perf_counter()
-    X, Y = [], []
-    for w, seed in members:
-        s = clusters.water_cluster(w, seed)
-        with binding.Handle(s) as hh:
-            if precision is None:
-                hh.scf()
-            else:
-                hh.scf(precision=precision, slices=3, incremental=1, approx_diag=1)
-            Y.append(hh.water_blocks(hh.matrix("D")))
-        X.append(binding.water_features(s))
+    systems = [clusters.water_cluster(w, seed) for w, seed in members]
+    X = [binding.water_features(s) for s in systems]
+    Y = [None] * len(systems)
+
+    def keep(k, hh, res):
+        if not res["converged"]:
+            raise RuntimeError(f"training cluster {members[k]} did not converge")
+        Y[k] = hh.water_blocks(hh.matrix("D"))
+
+    # the converged densities come from the batched SCF, in waves planned against the free device memory
+    free, _ = torch.cuda.mem_get_info()
+    binding.scf_waves(systems, int(0.5 * free), precision=binding.DF_PREC_FP64 if precision is None else precision,
+                      slices=3, on_done=keep, **({} if precision is None else dict(incremental=1, approx_diag=1)))
     t_data = time.perf_counter() - t0
     X, Y = np.concatenate(X), np.concatenate(Y)
     nout = Y.shape[1]

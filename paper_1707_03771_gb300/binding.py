@@ -431,9 +431,10 @@ def estimate_bytes(system, precision=DF_PREC_FP64, slices=5) -> int:
     return int(total)
 
 
-def scf_waves(systems, budget_bytes, precision=DF_PREC_FP64, slices=3, **kw):
+def scf_waves(systems, budget_bytes, precision=DF_PREC_FP64, slices=3, on_done=None, **kw):
     """Solve many molecules in waves whose estimated device memory fits `budget_bytes`; each wave is
-    one scf_run_batch. Returns one result dict per system, in order."""
+    one scf_run_batch. on_done(index, handle, result), if given, is called for every molecule before its
+    handle is closed. Returns one result dict per system, in order."""
     results = [None] * len(systems)
     order = list(range(len(systems)))
     i = 0
@@ -449,6 +450,9 @@ def scf_waves(systems, budget_bytes, precision=DF_PREC_FP64, slices=3, **kw):
         handles = [Handle(systems[k]) for k in wave]
         try:
             res = scf_batch(handles, precision=precision, slices=slices, **kw)
+            if on_done is not None:
+                for k, hd, r in zip(wave, handles, res):
+                    on_done(k, hd, r)
         finally:
             for h in handles:
                 h.close()

@@ -336,7 +336,8 @@ namespace {
 // full or incremental exchange). A kind is launched directly the first time it occurs (buffers are sized and
 // tile choices made then), captured from the stream the second time and replayed from then on; the sequence
 // reads everything that changes between iterations (the DIIS slot) from device memory. A sequence that
-// cannot be captured (a call that is not allowed in stream capture) is marked and launched directly.
+// cannot be captured (a call that is not allowed in stream capture) is marked and launched directly;
+// sequences that call cuSOLVER are not offered for capture at all.
 class GraphCache {
   public:
     ~GraphCache() { clear(); }
@@ -546,8 +547,12 @@ class ScfRun {
         if (first_factor_) {
             if (m0_ > nocc_) first_factor_jk();
             else jk_dispatch(h_, h_->Dm.p, h_->dC.p, m0_, h_->dJ.p, h_->dK.p, o_.precision, slices_);
+        } else if (inc) {
+            // the incremental build calls cuSOLVER (QR and the small eigenproblem), which is not captured: a
+            // refused capture left the solver unusable for the direct launch that follows
+            jk_device(inc, ref);
         } else {
-            const int kind = ((o_.precision == DF_PREC_SPLIT ? slices_ : 0) << 2) | (inc ? 2 : (ref ? 1 : 0));
+            const int kind = ((o_.precision == DF_PREC_SPLIT ? slices_ : 0) << 2) | (ref ? 1 : 0);
             graphs_.run(s_, kind, [&] { jk_device(inc, ref); });
         }
         if (inc) {
