@@ -552,6 +552,7 @@ def guess_study(args):
     evals = [(8 + min(24, int(rng.uniform() * 25)), 20000 + k) for k in range(n_eval)]
     prec = binding.DF_PREC_SPLIT
     net, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
+    print(json.dumps({"training": summary}), file=sys.stderr, flush=True)
     rows = []
     for w, seed in evals:
         with binding.Handle(clusters.water_cluster(w, seed)) as h:
@@ -569,6 +570,7 @@ def guess_study(args):
                      "dE_learned_vs_core": lrn["energy"] - core["energy"],
                      "dE_sad_vs_core": sadr["energy"] - core["energy"],
                      "converged": bool(core["converged"] and lrn["converged"] and sadr["converged"])})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)   # progress, one line per held-out cluster
     net.close()
     it_c = [r["iterations_core"] for r in rows]
     it_s = [r["iterations_sad"] for r in rows]
