@@ -124,7 +124,7 @@ def _peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel and tile on the same workload;
 # keyed by (workload, kernel, slices, tile width). Anything not captured reports null.
-NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.588e9 + 8.975e9, ("water32", "K", 5, 32): 72.219e9 + 0.044e9}
+NCU_TRAFFIC = {}
 
 def core_density(h):
     """A physical density for the timed builds: the core-Hamiltonian orbitals of the handle's molecule."""
@@ -551,10 +551,24 @@ def guess_study(args):
     train = [(4 + min(20, int(rng.uniform() * 21)), 10000 + k) for k in range(n_train)]
     evals = [(8 + min(24, int(rng.uniform() * 25)), 20000 + k) for k in range(n_eval)]
     prec = binding.DF_PREC_SPLIT
-    net, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
+    if args.guess_net and os.path.exists(args.guess_net):
+        # a network saved by an earlier run of the same study (same training set and epochs)
+        with np.load(args.guess_net) as f:
+            summary = json.loads(str(f["summary"]))
+            if summary["train_clusters"] != n_train or summary["epochs"] != args.guess_epochs:
+                raise SystemExit(f"{args.guess_net} holds a network trained on {summary['train_clusters']} "
+                                 f"clusters for {summary['epochs']} epochs")
+            net = binding.Mlp(binding.DF_MLP_NFEAT, 256, 3, int(f["nout"]), seed=7)
+            net.set_params(f["params"])
+        summary["loaded_from_file"] = True
+    else:
+        net, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
+        if args.guess_net:
+            np.savez(args.guess_net, params=net.params(), nout=net.nout, summary=json.dumps(summary))
     print(json.dumps({"training": summary}), file=sys.stderr, flush=True)
+    lo, hi = (int(x) for x in args.guess_eval_range.split(":")) if args.guess_eval_range else (0, n_eval)
     rows = []
-    for w, seed in evals:
+    for w, seed in evals[lo:hi]:
         with binding.Handle(clusters.water_cluster(w, seed)) as h:
             h.build_B()
             core = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1)
@@ -576,7 +590,7 @@ def guess_study(args):
     it_s = [r["iterations_sad"] for r in rows]
     it_l = [r["iterations_learned"] for r in rows]
     print(json.dumps({"study": "learned initial guess on held-out clusters", "training": summary,
-                      "eval_clusters": n_eval, "mean_iterations_core": float(np.mean(it_c)),
+                      "eval_clusters": n_eval, "eval_range": [lo, hi], "mean_iterations_core": float(np.mean(it_c)),
                       "mean_iterations_sad": float(np.mean(it_s)),
                       "mean_iterations_learned": float(np.mean(it_l)),
                       "iterations_saved_vs_core": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
@@ -760,6 +774,10 @@ def main():
     ap.add_argument("--guess-study", default=None, metavar="NTRAIN,NEVAL",
                     help="only the learned-guess study on held-out clusters (one JSON line)")
     ap.add_argument("--guess-epochs", type=int, default=200)
+    ap.add_argument("--guess-net", default=None, metavar="NPZ",
+                    help="guess study: load the trained network from this file if it exists, else save it there")
+    ap.add_argument("--guess-eval-range", default=None, metavar="LO:HI",
+                    help="guess study: evaluate only held-out clusters LO..HI-1")
     ap.add_argument("--learned", type=int, default=32, help="training clusters for the learned guess (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
