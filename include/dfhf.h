@@ -208,6 +208,18 @@ int df_sad_density(df_handle* h, double* D0);
  * approx_diag 0. After the run df_get_matrix gives the total density (6) and the spin densities (12, 13). */
 int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_result* out);
 
+/* Restricted open-shell Hartree-Fock (same section of the paper: ROHF on the density-fitted Fock builder):
+ * one orbital set, nbeta closed, nalpha - nbeta open, D_a / D_b from the first nalpha / nbeta orbitals,
+ * F_s and E as in scf_run_uhf. Each step diagonalises the effective Fock matrix in the basis of the current
+ * orbitals: closed-open blocks F_b, open-virtual blocks F_a, all other blocks (F_a + F_b)/2, plus
+ * level_shift on the virtual and level_shift/2 on the open diagonal (the shift does not move the converged
+ * energy; 0.5 Eh is a safe value, 0 can oscillate). DIIS over the effective matrix in the orthogonal basis
+ * with its off-diagonal class blocks (proportional to the orbital gradient) as the error; convergence as
+ * scf_run. out->s2 = S(S+1) up to rounding. Arguments, options and errors as scf_run_uhf; DF_E_ARG for a
+ * negative or non-finite level_shift. */
+int scf_run_rohf(df_handle* h, const df_options* opts, int nalpha, int nbeta, double level_shift,
+                 df_result* out);
+
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
  * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric
  * (eigenvectors of X^T S D0 S X). Otherwise as scf_run. */

@@ -23,7 +23,7 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
             "df_fp64_rate", "df_sad_density", "df_build_B_batch",
-            "df_init_open", "scf_run_uhf"]
+            "df_init_open", "scf_run_uhf", "scf_run_rohf"]
 DF_MLP_NFEAT = 57
 
 
@@ -90,6 +90,7 @@ def load(path: str | None = None):
     L.df_build_B_batch.argtypes = [P(c_void_p), c_int, c_double, c_int, c_int]
     L.df_init_open.argtypes = [P(Atom), c_int, P(Shell), c_int, P(Shell), c_int, c_int, P(c_void_p)]
     L.scf_run_uhf.argtypes = [c_void_p, P(Options), c_int, c_int, P(Result)]
+    L.scf_run_rohf.argtypes = [c_void_p, P(Options), c_int, c_int, ctypes.c_double, P(Result)]
     L.df_coulomb_noalloc.argtypes = [c_void_p, c_void_p, c_void_p]
     L.df_scf_history.argtypes = [c_void_p, dp, c_int]
     L.scf_run_batch.argtypes = [P(c_void_p), c_int, P(Options), P(Result)]
@@ -248,6 +249,17 @@ class Handle:
         rc = load().scf_run_uhf(self.h, ctypes.byref(o), int(nalpha), int(nbeta), ctypes.byref(r))
         if rc not in (DF_OK, DF_E_NOTCONV):
             self._check(rc, "scf_run_uhf")
+        return r.as_dict()
+
+    def scf_rohf(self, nalpha, nbeta, level_shift=0.5, conv_E=1e-10, conv_err=1e-7, max_iter=200, diis_size=8,
+                 precision=DF_PREC_FP64, slices=3, screen_tau=0.0):
+        """Restricted open-shell Hartree-Fock (scf_run_rohf): nbeta closed and nalpha - nbeta open orbitals."""
+        o = Options(conv_E, conv_err, max_iter, diis_size, DF_GUESS_CORE, precision, slices, 0, screen_tau, 0)
+        r = Result()
+        rc = load().scf_run_rohf(self.h, ctypes.byref(o), int(nalpha), int(nbeta), float(level_shift),
+                                 ctypes.byref(r))
+        if rc not in (DF_OK, DF_E_NOTCONV):
+            self._check(rc, "scf_run_rohf")
         return r.as_dict()
 
     def sad_density(self):

@@ -667,6 +667,26 @@ int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_
     }
 }
 
+int scf_run_rohf(df_handle* h, const df_options* opts, int nalpha, int nbeta, double level_shift, df_result* out) {
+    if (!h || !opts || !out) return DF_E_ARG;
+    if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
+    if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
+    if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
+    if (!(level_shift >= 0.0) || !std::isfinite(level_shift))
+        return fail(h, Error{DF_E_ARG, "scf_run_rohf: the level shift must be finite and >= 0"});
+    if (opts->guess != DF_GUESS_CORE || opts->incremental || opts->approx_diag)
+        return fail(h, Error{DF_E_ARG, "scf_run_rohf: core-Hamiltonian guess, full builds and full eigensolves only"});
+    if (nalpha < nbeta || nbeta < 0 || nalpha + nbeta != h->nelec || nalpha > h->n)
+        return fail(h, Error{DF_E_ARG, "scf_run_rohf: need nalpha >= nbeta >= 0, nalpha + nbeta = electron count"});
+    try {
+        DF_CUDA(cudaSetDevice(h->device));
+        return scf_drive_rohf(h, opts, nalpha, nbeta, level_shift, out);
+    } catch (const Error& e) {
+        out->status = e.code;
+        return fail(h, e);
+    }
+}
+
 int df_get_rows(df_handle* h, int which, int p0, int count, double* out) {
     if (!h || !out || p0 < 0 || count < 1 || p0 + count > h->naux || (which != 0 && which != 1)) return DF_E_ARG;
     const double* src = which == 0 ? h->A3c.p : h->B.p;

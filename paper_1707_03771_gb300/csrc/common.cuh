@@ -225,6 +225,7 @@ std::vector<double> aufbau_occupations(const std::vector<double>& eps, double ne
 void sad_factor(df_handle* h, DevBuf<double>& C0, int& m0);
 int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs);
 int scf_drive_uhf(df_handle* h, const df_options* o, int nalpha, int nbeta, df_result* r);
+int scf_drive_rohf(df_handle* h, const df_options* o, int nalpha, int nbeta, double level_shift, df_result* r);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
 

@@ -135,14 +135,16 @@ __global__ void absmax_kernel(const double* __restrict__ x, long long len, doubl
     if (threadIdx.x == 0) *out = sm[0];
 }
 
-// DIIS: Bm[slot][j] = Bm[j][slot] = <e_slot, e_j> for the vectors present (one block per j)
-__global__ void diis_dots_kernel(const double* __restrict__ E, long long len, const int* __restrict__ slotp,
-                                 const int* __restrict__ present, int size, double* __restrict__ Bm) {
+// DIIS: Bm[slot][j] = Bm[j][slot] = <e_slot, e_j> for the vectors present (one block per j); vectors of
+// len elements, `stride` apart
+__global__ void diis_dots_kernel(const double* __restrict__ E, long long stride, long long len,
+                                 const int* __restrict__ slotp, const int* __restrict__ present, int size,
+                                 double* __restrict__ Bm) {
     const int j = blockIdx.x;
     const int slot = *slotp;
     if (!present[j]) return;
-    const double* a = E + (long long)slot * len;
-    const double* b = E + (long long)j * len;
+    const double* a = E + (long long)slot * stride;
+    const double* b = E + (long long)j * stride;
     double s = 0;
     for (long long i = threadIdx.x; i < len; i += blockDim.x) s = fma(a[i], b[i], s);
     __shared__ double sm[256];
@@ -203,13 +205,14 @@ __global__ void diis_solve_kernel(const double* __restrict__ Bm, const int* __re
     *status = 0;
 }
 
-// Fx = sum_i coef[slot_i] F_slot_i
-__global__ void diis_combine_kernel(const double* __restrict__ Fs, long long len, const int* __restrict__ slots, int m,
-                                    const double* __restrict__ coef, double* __restrict__ Fx) {
+// Fx = sum_i coef[slot_i] F_slot_i (vectors of len elements, `stride` apart)
+__global__ void diis_combine_kernel(const double* __restrict__ Fs, long long stride, long long len,
+                                    const int* __restrict__ slots, int m, const double* __restrict__ coef,
+                                    double* __restrict__ Fx) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
     double s = 0;
-    for (int k = 0; k < m; ++k) s = fma(coef[slots[k]], Fs[(long long)slots[k] * len + i], s);
+    for (int k = 0; k < m; ++k) s = fma(coef[slots[k]], Fs[(long long)slots[k] * stride + i], s);
     Fx[i] = s;
 }
 
@@ -682,7 +685,8 @@ class ScfRun {
         for (int q = 0; q < DIIS_MAX; ++q) pin_ctl_[q] = present_[q];
         for (size_t q = 0; q < order_.size(); ++q) pin_ctl_[DIIS_MAX + q] = order_[q];
         DF_CUDA(cudaMemcpyAsync(d_ints_, pin_ctl_, sizeof(int) * 2 * DIIS_MAX, cudaMemcpyHostToDevice, s_));
-        diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, d_slot_, d_ints_, DIIS_MAX, d_B_);
+        diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(h_->diisE.p, (long long)nX_ * nX_, (long long)nX_ * nX_, d_slot_,
+                                                   d_ints_, DIIS_MAX, d_B_);
         DF_CHECK_LAUNCH();
         // Roothaan step: a full eigensolve, or late (options.approx_diag) a rotation of the previous
         // orbitals, with a full eigensolve every DIAG_RESET late iterations
@@ -693,7 +697,7 @@ class ScfRun {
             diis_solve_kernel<<<1, 1, 0, s_>>>(d_B_, d_ints_ + DIIS_MAX, (int)order_.size(), d_coef_,
                                                d_ints_ + 2 * DIIS_MAX);
             DF_CHECK_LAUNCH();
-            diis_combine_kernel<<<nblk(no), 256, 0, s_>>>(h_->diisF.p, no, d_ints_ + DIIS_MAX, (int)order_.size(),
+            diis_combine_kernel<<<nblk(no), 256, 0, s_>>>(h_->diisF.p, no, no, d_ints_ + DIIS_MAX, (int)order_.size(),
                                                          d_coef_, Fx);
             DF_CHECK_LAUNCH();
         } else {
@@ -1009,9 +1013,31 @@ class ScfRun {
 // over the stacked pair (F'_a, F'_b) with errors F'_s P_s - P_s F'_s (P_s = V_s,occ V_s,occ^T; the
 // orthogonal-basis form of X^T (F_s D_s S - S D_s F_s) X), one set of coefficients for both spins;
 // core-Hamiltonian start for both spins; every step on the device in FP64 except the exchange contraction.
+// Restricted open-shell effective Fock matrix in the basis of the current orbitals (closed p < nb, open
+// nb <= p < na, virtual p >= na): closed-open pairs take F_b, open-virtual pairs F_a, all others
+// (F_a + F_b) / 2. Fa_mo becomes the effective matrix plus the level shift (lambda on the virtual,
+// lambda / 2 on the open diagonal), Fb_mo its off-diagonal class blocks (the DIIS error).
+__global__ void rohf_effective_kernel(double* __restrict__ Fa_mo, double* __restrict__ Fb_mo, int m, int na, int nb,
+                                      double shift) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * m) return;
+    const int p = (int)(idx / m), q = (int)(idx % m);
+    const int cp = p < nb ? 0 : (p < na ? 1 : 2), cq = q < nb ? 0 : (q < na ? 1 : 2);
+    const double fa = Fa_mo[idx], fb = Fb_mo[idx];
+    double f = 0.5 * (fa + fb);
+    if (cp + cq == 1) f = fb;                       // closed-open
+    else if (cp + cq == 3) f = fa;                  // open-virtual
+    Fb_mo[idx] = cp != cq ? f : 0.0;
+    if (p == q) f += cp == 2 ? shift : (cp == 1 ? 0.5 * shift : 0.0);
+    Fa_mo[idx] = f;
+}
+
+// Unrestricted (two orbital sets) or restricted open-shell (one set: the beta orbitals are the first nb
+// alpha orbitals) Hartree-Fock on the density-fitted builds.
 class UhfRun {
   public:
-    UhfRun(df_handle* h, const df_options* o, int na, int nb, df_result* r) : h_(h), o_(*o), r_(r), na_(na), nb_(nb) {}
+    UhfRun(df_handle* h, const df_options* o, int na, int nb, df_result* r, bool restricted = false, double shift = 0.0)
+        : h_(h), o_(*o), r_(r), na_(na), nb_(nb), ro_(restricted), shift_(shift) {}
     ~UhfRun() { release(); }
 
     int run() {
@@ -1052,6 +1078,7 @@ class UhfRun {
         build_x_kernel<<<nblk((long long)n_ * nX_), 256, 0, s_>>>(h_->work1.p, h_->eps.p, n_, first, nX_, h_->X.p);
         DF_CHECK_LAUNCH();
         const long long no = (long long)nX_ * nX_;
+        const long long vlen = ro_ ? no : 2 * no;   // DIIS vector: both spins' matrices, or the effective one
         ensure_jk_buffers(h_, std::max(na_, 1));
         auto dalloc = [](double** p, long long count) { DF_CUDA(cudaMalloc((void**)p, sizeof(double) * count)); };
         dalloc(&D_, 3 * nn_);               // D_a | D_b | D_a + D_b
@@ -1107,7 +1134,23 @@ class UhfRun {
                 present[slot] = 0;
             }
             double* E = diisE_ + (long long)slot * 2 * no;
-            for (int sp = 0; sp < 2; ++sp) {
+            if (ro_) {
+                // F_s in the orbital basis (V: current orbitals as rows), the effective matrix and its error,
+                // both taken back to the orthogonal basis: F'_eff = V^T F_eff,mo V
+                for (int sp = 0; sp < 2; ++sp) {
+                    to_orth(F_ + sp * nn_, Fo_ + sp * no);
+                    dgemm(s_, false, false, nX_, nX_, nX_, 1.0, V_, nX_, Fo_ + sp * no, nX_, 0.0, h_->work1.p, nX_);
+                    dgemm(s_, false, true, nX_, nX_, nX_, 1.0, h_->work1.p, nX_, V_, nX_, 0.0,
+                          sp == 0 ? h_->work2.p : h_->work3.p, nX_);
+                }
+                rohf_effective_kernel<<<nblk(no), 256, 0, s_>>>(h_->work2.p, h_->work3.p, nX_, na_, nb_, shift_);
+                DF_CHECK_LAUNCH();
+                dgemm(s_, true, false, nX_, nX_, nX_, 1.0, V_, nX_, h_->work2.p, nX_, 0.0, h_->work1.p, nX_);
+                dgemm(s_, false, false, nX_, nX_, nX_, 1.0, h_->work1.p, nX_, V_, nX_, 0.0, Fo_, nX_);
+                dgemm(s_, true, false, nX_, nX_, nX_, 1.0, V_, nX_, h_->work3.p, nX_, 0.0, h_->work1.p, nX_);
+                dgemm(s_, false, false, nX_, nX_, nX_, 1.0, h_->work1.p, nX_, V_, nX_, 0.0, E, nX_);
+            }
+            for (int sp = 0; sp < 2 && !ro_; ++sp) {
                 const int nocc = sp == 0 ? na_ : nb_;
                 double* Fos = Fo_ + sp * no;
                 to_orth(F_ + sp * nn_, Fos);
@@ -1121,7 +1164,7 @@ class UhfRun {
                     DF_CUDA(cudaMemsetAsync(E + sp * no, 0, sizeof(double) * no, s_));
                 }
             }
-            absmax_kernel<<<1, 1024, 0, s_>>>(E, 2 * no, scal + 3);
+            absmax_kernel<<<1, 1024, 0, s_>>>(E, vlen, scal + 3);
             DF_CHECK_LAUNCH();
             DF_CUDA(cudaMemcpyAsync(pin_, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s_));
             DF_CUDA(cudaStreamSynchronize(s_));
@@ -1155,7 +1198,7 @@ class UhfRun {
                 for (int q : order) present[q] = 0;
                 order.clear();
             }
-            DF_CUDA(cudaMemcpyAsync(diisF_ + (long long)slot * 2 * no, Fo_, sizeof(double) * 2 * no,
+            DF_CUDA(cudaMemcpyAsync(diisF_ + (long long)slot * 2 * no, Fo_, sizeof(double) * vlen,
                                     cudaMemcpyDeviceToDevice, s_));
             present[slot] = 1;
             order.push_back(slot);
@@ -1163,13 +1206,13 @@ class UhfRun {
             for (size_t q = 0; q < order.size(); ++q) ctl[DIIS_MAX + q] = order[q];
             ctl[2 * DIIS_MAX + 3] = slot;
             DF_CUDA(cudaMemcpyAsync(ints_, ctl.data(), sizeof(int) * (2 * DIIS_MAX + 4), cudaMemcpyHostToDevice, s_));
-            diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(diisE_, 2 * no, slotp, ints_, DIIS_MAX, Bm_);
+            diis_dots_kernel<<<DIIS_MAX, 256, 0, s_>>>(diisE_, 2 * no, vlen, slotp, ints_, DIIS_MAX, Bm_);
             DF_CHECK_LAUNCH();
             if (it >= 2 && order.size() >= 2) {
                 diis_solve_kernel<<<1, 1, 0, s_>>>(Bm_, ints_ + DIIS_MAX, (int)order.size(), coef, ints_ + 2 * DIIS_MAX);
                 DF_CHECK_LAUNCH();
-                diis_combine_kernel<<<nblk(2 * no), 256, 0, s_>>>(diisF_, 2 * no, ints_ + DIIS_MAX, (int)order.size(),
-                                                                 coef, Fo_);
+                diis_combine_kernel<<<nblk(vlen), 256, 0, s_>>>(diisF_, 2 * no, vlen, ints_ + DIIS_MAX,
+                                                                 (int)order.size(), coef, Fo_);
                 DF_CHECK_LAUNCH();
                 int singular = 0;
                 DF_CUDA(cudaMemcpyAsync(&singular, ints_ + 2 * DIIS_MAX, sizeof(int), cudaMemcpyDeviceToHost, s_));
@@ -1206,8 +1249,14 @@ class UhfRun {
         const long long no = (long long)nX_ * nX_;
         for (int sp = 0; sp < 2; ++sp) {
             const int nocc = sp == 0 ? na_ : nb_;
-            DF_CUDA(cudaMemcpyAsync(V_ + sp * no, Fs + sp * no, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
-            eig(V_ + sp * no, nX_, h_->eps.p + sp * n_);
+            if (ro_ && sp == 1) {
+                // one orbital set: the beta determinant takes the first nb orbitals of the alpha step
+                DF_CUDA(cudaMemcpyAsync(V_ + no, V_, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+                DF_CUDA(cudaMemcpyAsync(h_->eps.p + n_, h_->eps.p, sizeof(double) * nX_, cudaMemcpyDeviceToDevice, s_));
+            } else {
+                DF_CUDA(cudaMemcpyAsync(V_ + sp * no, Fs + sp * no, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+                eig(V_ + sp * no, nX_, h_->eps.p + sp * n_);
+            }
             double* C = C_ + (sp == 0 ? 0 : (long long)n_ * na_);
             double* D = D_ + sp * nn_;
             if (nocc > 0) {
@@ -1272,6 +1321,8 @@ class UhfRun {
     df_options o_;
     df_result* r_;
     int na_, nb_;
+    bool ro_;
+    double shift_;
     int n_ = 0, nX_ = 0, slices_ = 3, lwork_ = 0;
     long long nn_ = 0;
     cudaStream_t s_ = nullptr;
@@ -1313,6 +1364,11 @@ void atomic_scf(df_handle* ha, double nelec, std::vector<double>& Cw, int& m) {
 
 int scf_drive_uhf(df_handle* h, const df_options* o, int nalpha, int nbeta, df_result* r) {
     UhfRun run(h, o, nalpha, nbeta, r);
+    return run.run();
+}
+
+int scf_drive_rohf(df_handle* h, const df_options* o, int nalpha, int nbeta, double level_shift, df_result* r) {
+    UhfRun run(h, o, nalpha, nbeta, r, true, level_shift);
     return run.run();
 }
 

@@ -1,7 +1,8 @@
 """DF-UHF on the GPU (scf_run_uhf) against the oracle (oracle/dfuhf.py): the closed-shell reduction to the RHF
 energy, the one-electron hydrogen atom (lowest eigenvalue of the core Hamiltonian, <S^2> = 3/4), and the
 doublet cation and triplet of the 2-water cluster, energy, <S^2> and spin densities element by element;
-the split-precision exchange within 1e-6 Eh."""
+the split-precision exchange within 1e-6 Eh. DF-ROHF (scf_run_rohf) against oracle/dfrohf.py the same way,
+with <S^2> = S(S+1) and E_UHF <= E_ROHF."""
 import numpy as np
 import pytest
 
@@ -66,3 +67,43 @@ def test_open_shell_against_oracle(lib, water2, charge, na, nb):
     assert abs(u["s2"] - ref.s2) <= 1e-6
     assert np.abs(Da - ref.Da).max() <= 1e-6 and np.abs(Db - ref.Db).max() <= 1e-6
     assert abs(us["energy"] - u["energy"]) <= 1e-6
+
+
+@pytest.mark.parametrize("charge,na,nb", [(1, 10, 9), (0, 11, 9)])
+def test_rohf_against_oracle(lib, water2, charge, na, nb):
+    """ROHF (scf_run_rohf) against oracle/dfrohf.py on the same FP64 B: energy, <S^2> = S(S+1), spin
+    densities; above the UHF energy; the split-precision exchange within 1e-6 Eh; closed shell = RHF."""
+    import copy
+
+    from oracle import dfrhf, dfrohf
+    system = copy.deepcopy(water2)
+    system.charge = charge
+    ref = dfrohf.rohf(system, na, nb)
+    assert ref.converged
+    with lib.Handle(system, open_shell=True) as h:
+        h.build_B(whitening=lib.DF_WHITEN_FP64)
+        ro = h.scf_rohf(na, nb)
+        Da, Db = h.matrix("Da"), h.matrix("Db")
+        u = h.scf_uhf(na, nb)
+        rs = h.scf_rohf(na, nb, precision=lib.DF_PREC_SPLIT, slices=3)
+        with pytest.raises(lib.DFError) as e:
+            h.scf_rohf(na, nb, level_shift=-1.0)
+        assert e.value.code == lib.DF_E_ARG
+    S = 0.5 * (na - nb)
+    print(f"ROHF charge {charge} ({na}, {nb}): GPU {ro['energy']:.10f} ({ro['iterations']} it), oracle "
+          f"{ref.energy:.10f} ({ref.iterations} it), UHF {u['energy']:.10f}; <S^2> {ro['s2']:.8f}; "
+          f"split {rs['energy'] - ro['energy']:+.2e}")
+    assert ro["converged"] and rs["converged"]
+    assert abs(ro["energy"] - ref.energy) <= 1e-9
+    assert abs(ro["s2"] - S * (S + 1)) <= 1e-9
+    assert np.abs(Da - ref.Da).max() <= 1e-6 and np.abs(Db - ref.Db).max() <= 1e-6
+    assert u["energy"] <= ro["energy"] + 1e-10
+    assert abs(rs["energy"] - ro["energy"]) <= 1e-6
+
+
+def test_closed_shell_rohf_equals_rhf(lib, water2):
+    with lib.Handle(water2) as h:
+        h.build_B()
+        r = h.scf()
+        ro = h.scf_rohf(10, 10)
+    assert ro["converged"] and abs(ro["energy"] - r["energy"]) <= 1e-9, (ro["energy"], r["energy"])

@@ -583,3 +583,90 @@ def test_uhf_hydrogen_atom_has_no_electron_interaction(water2_sys):
     e0 = eigh(dfrhf.core_hamiltonian(atom), dfrhf.overlap(atom), eigvals_only=True)[0]
     assert u.converged and abs(u.energy - e0) <= 1e-10, (u.energy, e0)
     assert abs(u.s2 - 0.75) <= 1e-12
+
+
+# restricted open-shell Hartree-Fock (oracle/dfrohf.py)
+
+def test_rohf_closed_shell_equals_rhf(water2_sys):
+    """With no open orbitals the effective Fock matrix is the closed-shell one: the RHF energy, <S^2> = 0."""
+    from oracle import dfrohf
+    n = water2_sys.n_electrons // 2
+    ro = dfrohf.rohf(water2_sys, n, n)
+    r = dfrhf.scf(water2_sys)
+    assert ro.converged and abs(ro.energy - r.energy) <= 1e-9, (ro.energy, r.energy)
+    assert abs(ro.s2) <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def water2_open(water2_sys):
+    """The 2-water cluster as a doublet cation (10, 9) and as a triplet (11, 9): ROHF and UHF of each."""
+    import copy
+
+    from oracle import dfrohf, dfuhf
+    out = {}
+    for charge, na, nb in [(1, 10, 9), (0, 11, 9)]:
+        s = copy.deepcopy(water2_sys)
+        s.charge = charge
+        B = dfrhf.whiten(dfrhf.three_center(s), dfrhf.metric(s))
+        out[(na, nb)] = (s, B, dfrohf.rohf(s, na, nb, B=B, conv_err=1e-9), dfuhf.uhf(s, na, nb, B=B))
+    return out
+
+
+@pytest.mark.parametrize("na,nb", [(10, 9), (11, 9)])
+def test_rohf_is_a_spin_eigenfunction_above_uhf(water2_open, na, nb):
+    """ROHF: <S^2> = S(S+1) exactly (the beta orbitals are a subset of the alpha ones); the UHF determinant
+    has more variational freedom, so E_UHF <= E_ROHF, and UHF is spin-contaminated above S(S+1)."""
+    s, B, ro, u = water2_open[(na, nb)]
+    S = 0.5 * (na - nb)
+    assert ro.converged and u.converged
+    assert abs(ro.s2 - S * (S + 1)) <= 1e-10, ro.s2
+    assert u.energy <= ro.energy + 1e-10 and ro.energy - u.energy < 0.05, (u.energy, ro.energy)
+    assert u.s2 > S * (S + 1)
+
+
+@pytest.mark.parametrize("na,nb", [(10, 9), (11, 9)])
+def test_rohf_converged_orbitals_are_stationary(water2_open, na, nb):
+    """The converged ROHF orbitals are a stationary point of the energy under every orbital rotation
+    C -> C exp(k): central differences of E along random antisymmetric k vanish to O(t^2), while the same
+    differences at the core-Hamiltonian orbitals match the analytic gradient (which pins the coupling
+    blocks: F_b on closed-open, F_a on open-virtual, F_a + F_b on closed-virtual)."""
+    from scipy.linalg import expm
+
+    from oracle import dfrohf
+    s, B, ro, _ = water2_open[(na, nb)]
+    H = dfrhf.core_hamiltonian(s)
+    e_nuc = dfrhf.nuclear_repulsion(s.atoms)
+    X, _ = dfrhf.canonical_orthogonalizer(dfrhf.overlap(s))
+    rng = np.random.default_rng(5)
+
+    def energy(C):
+        return dfrohf.uhf_functional(s, B, H, C, na, nb, e_nuc)[0]
+
+    Ccore = X @ np.linalg.eigh(X.T @ H @ X)[1]
+    nmo = Ccore.shape[1]
+    t = 1e-4
+    for _ in range(3):
+        k = rng.normal(size=(nmo, nmo))
+        k = np.triu(k, 1) - np.triu(k, 1).T
+        k /= np.linalg.norm(k)
+        # stationary at convergence (converged to max|e| < 1e-9: the directional derivative along a unit
+        # rotation is at most |G|_F, a few 1e-8), and a minimum along k
+        ep, em, e0 = energy(ro.C @ expm(t * k)), energy(ro.C @ expm(-t * k)), energy(ro.C)
+        dE = (ep - em) / (2 * t)
+        curv = (ep + em - 2 * e0) / t**2
+        assert abs(dE) <= 1e-6 and curv > 0.0, (dE, curv)
+        # analytic gradient at the core-Hamiltonian orbitals
+        _, Fa, Fb, _, _ = dfrohf.uhf_functional(s, B, H, Ccore, na, nb, e_nuc)
+        G = dfrohf.orbital_gradient(Ccore.T @ Fa @ Ccore, Ccore.T @ Fb @ Ccore, na, nb)
+        fd = (energy(Ccore @ expm(t * k)) - energy(Ccore @ expm(-t * k))) / (2 * t)
+        an = float(np.sum(np.triu(G, 1) * np.triu(k, 1)))
+        assert abs(an) > 1e-2 and abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+    # the effective matrix's off-diagonal class blocks are the gradient up to the factors -2, -2, -4
+    _, Fa, Fb, _, _ = dfrohf.uhf_functional(s, B, H, Ccore, na, nb, e_nuc)
+    Fa_mo, Fb_mo = Ccore.T @ Fa @ Ccore, Ccore.T @ Fb @ Ccore
+    _, err = dfrohf.effective_fock_mo(Fa_mo, Fb_mo, na, nb)
+    G = dfrohf.orbital_gradient(Fa_mo, Fb_mo, na, nb)
+    cls = dfrohf.classes(nmo, na, nb)
+    for a, b, f in [(0, 1, -2.0), (1, 2, -2.0), (0, 2, -4.0)]:
+        blk = np.ix_(cls == a, cls == b)
+        assert np.abs(G[blk] - f * err[blk]).max() <= 1e-12 * max(1.0, np.abs(G[blk]).max())
