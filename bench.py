@@ -283,7 +283,7 @@ def gpu_arm(args):
             h.jk(D, np.ascontiguousarray(C[:, :7 * nw - nocc]), prec, 3)
         if guess_net is not None:
             t0 = time.perf_counter()
-            D0 = h.mlp_guess(guess_net, bf16=True)
+            D0 = guess_net.guess(h)
             t_guess = time.perf_counter() - t0
             learned["t_guess_s"] = t_guess
             runs.append(("split_learned" if split else "fp64_learned", prec, (D0, t_guess), inc))
@@ -486,7 +486,7 @@ def c2_measure(args, binding, clusters, lib, dev, stream, guess_net):
         out["dE_sad_vs_core"] = res_s["energy"] - res["energy"]
         if guess_net is not None:
             t1 = time.perf_counter()
-            D0 = h.mlp_guess(guess_net, bf16=True)
+            D0 = guess_net.guess(h)
             t_guess = time.perf_counter() - t1
             res_l = h.scf(precision=binding.DF_PREC_SPLIT, slices=3, incremental=1, approx_diag=1, guess=D0)
             out["ttc_split_learned_s"] = t_build + res_l["t_total_s"] + t_guess
@@ -495,19 +495,51 @@ def c2_measure(args, binding, clusters, lib, dev, stream, guess_net):
     return out
 
 
+class GuessNets:
+    """The learned guess's two networks: each water's diagonal block and the blocks of water pairs within
+    binding.PAIR_CUTOFF."""
+
+    def __init__(self, diag, pair):
+        self.diag, self.pair = diag, pair
+
+    def guess(self, h):
+        return h.mlp_guess(self.diag, bf16=True, pair_mlp=self.pair)
+
+    def close(self):
+        self.diag.close()
+        self.pair.close()
+
+
+def _fit(binding, X, Y, nin, epochs, batch, seed):
+    """A 256 x 3 ReLU network fitted to (X, Y), its last layer started at the mean target (zero weights)."""
+    nout = Y.shape[1]
+    net = binding.Mlp(nin, 256, 3, nout, seed=seed)
+    p = net.params()
+    p[-nout:] = Y.mean(axis=0)
+    p[-nout - nout * 256:-nout] = 0.0
+    net.set_params(p)
+    hist = net.train(X, Y, epochs=epochs, batch=batch, lr=3e-4, seed=seed + 1)
+    return net, hist
+
+
 def train_guess(binding, clusters, members, epochs=200, precision=None):
-    """Train the density-guess network on the converged densities of the seeded clusters `members`
-    ((waters, seed) pairs), generated by this library's SCF. Returns (network, summary)."""
+    """Train the density-guess networks on the converged densities of the seeded clusters `members`
+    ((waters, seed) pairs), generated by this library's SCF. Returns (GuessNets, summary)."""
     import torch
     t0 = time.perf_counter()
     systems = [clusters.water_cluster(w, seed) for w, seed in members]
     X = [binding.water_features(s) for s in systems]
+    pair_lists = [binding.water_pairs(s) for s in systems]
     Y = [None] * len(systems)
+    YP = [None] * len(systems)
 
     def keep(k, hh, res):
         if not res["converged"]:
             raise RuntimeError(f"training cluster {members[k]} did not converge")
-        Y[k] = hh.water_blocks(hh.matrix("D"))
+        D = hh.matrix("D")
+        Y[k] = hh.water_blocks(D)
+        pairs = pair_lists[k][0]
+        YP[k] = hh.pair_blocks(D, pairs).reshape(len(pairs), -1)
 
     # the converged densities come from the batched SCF, in waves planned against the free device memory
     free, _ = torch.cuda.mem_get_info()
@@ -515,19 +547,23 @@ def train_guess(binding, clusters, members, epochs=200, precision=None):
                       slices=3, on_done=keep, **({} if precision is None else dict(incremental=1, approx_diag=1)))
     t_data = time.perf_counter() - t0
     X, Y = np.concatenate(X), np.concatenate(Y)
-    nout = Y.shape[1]
-    net = binding.Mlp(binding.DF_MLP_NFEAT, 256, 3, nout, seed=7)
-    p = net.params()
-    p[-nout:] = Y.mean(axis=0)               # start from the mean water block (zero last-layer weights)
-    p[-nout - nout * 256:-nout] = 0.0
-    net.set_params(p)
+    XP = np.concatenate([pl[1] for pl in pair_lists])
+    YP = np.concatenate(YP)
     t0 = time.perf_counter()
-    hist = net.train(X, Y, epochs=epochs, batch=16, lr=3e-4, seed=3)
+    net, hist = _fit(binding, X, Y, binding.DF_MLP_NFEAT, epochs, 16, 7)
+    # the pair network sees about 3 samples per water: larger batches, and at most about 60000 steps
+    ep_pair = int(min(epochs, max(10, 60000 * 64 // max(1, len(XP)))))
+    pnet, hist_p = _fit(binding, XP, YP, binding.DF_MLP_NPFEAT, ep_pair, 64, 17)
     t_train = time.perf_counter() - t0
-    return net, {"train_clusters": len(members), "train_waters": int(sum(w for w, _ in members)),
-                 "train_samples": int(len(X)), "network": "57-256x3-1275 ReLU, FP32 weights, BF16 inference",
-                 "epochs": epochs, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
-                 "t_data_s": t_data, "t_train_s": t_train}
+    nbw = int(round(np.sqrt(YP.shape[1])))
+    return GuessNets(net, pnet), {
+        "train_clusters": len(members), "train_waters": int(sum(w for w, _ in members)),
+        "train_samples": int(len(X)), "network": f"57-256x3-{Y.shape[1]} ReLU, FP32 weights, BF16 inference",
+        "epochs": epochs, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+        "pair_cutoff_bohr": binding.PAIR_CUTOFF, "pair_samples": int(len(XP)),
+        "pair_network": f"{binding.DF_MLP_NPFEAT}-256x3-{nbw * nbw} ReLU, FP32 weights, BF16 inference",
+        "pair_epochs": ep_pair, "pair_loss_first": float(hist_p[0]), "pair_loss_last": float(hist_p[-1]),
+        "t_data_s": t_data, "t_train_s": t_train}
 
 
 def learned_guess_net(binding, clusters, n_train):
@@ -552,19 +588,23 @@ def guess_study(args):
     evals = [(8 + min(24, int(rng.uniform() * 25)), 20000 + k) for k in range(n_eval)]
     prec = binding.DF_PREC_SPLIT
     if args.guess_net and os.path.exists(args.guess_net):
-        # a network saved by an earlier run of the same study (same training set and epochs)
+        # networks saved by an earlier run of the same study (same training set and epochs)
         with np.load(args.guess_net) as f:
             summary = json.loads(str(f["summary"]))
             if summary["train_clusters"] != n_train or summary["epochs"] != args.guess_epochs:
-                raise SystemExit(f"{args.guess_net} holds a network trained on {summary['train_clusters']} "
+                raise SystemExit(f"{args.guess_net} holds networks trained on {summary['train_clusters']} "
                                  f"clusters for {summary['epochs']} epochs")
             net = binding.Mlp(binding.DF_MLP_NFEAT, 256, 3, int(f["nout"]), seed=7)
             net.set_params(f["params"])
+            pnet = binding.Mlp(binding.DF_MLP_NPFEAT, 256, 3, int(f["nout_pair"]), seed=17)
+            pnet.set_params(f["params_pair"])
+        nets = GuessNets(net, pnet)
         summary["loaded_from_file"] = True
     else:
-        net, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
+        nets, summary = train_guess(binding, clusters, train, epochs=args.guess_epochs, precision=prec)
         if args.guess_net:
-            np.savez(args.guess_net, params=net.params(), nout=net.nout, summary=json.dumps(summary))
+            np.savez(args.guess_net, params=nets.diag.params(), nout=nets.diag.nout, params_pair=nets.pair.params(),
+                     nout_pair=nets.pair.nout, summary=json.dumps(summary))
     print(json.dumps({"training": summary}), file=sys.stderr, flush=True)
     lo, hi = (int(x) for x in args.guess_eval_range.split(":")) if args.guess_eval_range else (0, n_eval)
     rows = []
@@ -574,7 +614,7 @@ def guess_study(args):
             core = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1)
             sadr = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess="sad")
             t0 = time.perf_counter()
-            D0 = h.mlp_guess(net, bf16=True)
+            D0 = nets.guess(h)
             t_guess = time.perf_counter() - t0
             lrn = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess=D0)
         rows.append({"waters": w, "seed": seed, "iterations_core": core["iterations"],
@@ -585,7 +625,7 @@ def guess_study(args):
                      "dE_sad_vs_core": sadr["energy"] - core["energy"],
                      "converged": bool(core["converged"] and lrn["converged"] and sadr["converged"])})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)   # progress, one line per held-out cluster
-    net.close()
+    nets.close()
     it_c = [r["iterations_core"] for r in rows]
     it_s = [r["iterations_sad"] for r in rows]
     it_l = [r["iterations_learned"] for r in rows]

@@ -230,7 +230,8 @@ int scf_run_guess(df_handle* h, const df_options* opts, const double* D0, df_res
  * frame: origin O, z along the H-O-H bisector, x along H1 - H2. A network maps DF_MLP_NFEAT
  * rotation-invariant features of the water's environment to the upper triangle of its diagonal density
  * block in that frame; blocks are rotated to the laboratory frame with real-solid-harmonic rotation
- * matrices and assembled block-diagonally. */
+ * matrices and assembled block-diagonally. A second network adds the blocks between nearby waters
+ * (df_mlp_guess_pairs). */
 #define DF_MLP_NFEAT 57
 typedef struct df_mlp df_mlp;
 
@@ -261,6 +262,24 @@ int df_water_blocks(df_handle* h, const double* D, float* out);
 int df_water_density(df_handle* h, const float* blocks, double* D0);
 /* Learned D0 (host n x n) for the handle's water cluster with network m (bf16 = BF16 inference). */
 int df_mlp_guess(df_handle* h, df_mlp* m, int bf16, double* D0);
+
+/* Pair blocks. An ordered pair (w1, w2) of waters whose O atoms are at most `cutoff` bohr apart has
+ * DF_MLP_NPFEAT features: the atoms of w2 in w1's frame relative to w1's O (/ 10 bohr), 5 bohr / r for the
+ * nine atom pairs between the waters, a Gaussian expansion of the O-O distance. Its block is the
+ * nb x nb block D[w1][w2] with both function sets rotated into w1's frame. */
+#define DF_MLP_NPFEAT 26
+/* The ordered pairs within cutoff (both orders, by w1 then w2): returns their number (or a DF_E_* code)
+ * and writes up to max_pairs of them (pairs: 2 ints each) and their features (feats: DF_MLP_NPFEAT floats
+ * each; may be NULL). max_pairs = 0 only counts. */
+int df_water_pairs(const df_atom* atoms, int natom, double cutoff, int* pairs, int max_pairs, float* feats);
+/* Frame blocks of the listed pairs of D (host n x n): out npairs x nb x nb floats, row-major. */
+int df_pair_blocks(df_handle* h, const double* D, const int* pairs, int npairs, float* out);
+/* Adds the laboratory-frame blocks of the listed pairs to D0 (host n x n) at [w1][w2] and, transposed, at
+ * [w2][w1]; a pair listed in both orders contributes the mean of its two blocks. */
+int df_pair_density(df_handle* h, const float* blocks, const int* pairs, int npairs, double* D0);
+/* df_mlp_guess with network m, plus the pair blocks of every pair within cutoff predicted by network mp
+ * (DF_MLP_NPFEAT inputs, nb * nb outputs). */
+int df_mlp_guess_pairs(df_handle* h, df_mlp* m, df_mlp* mp, double cutoff, int bf16, double* D0);
 
 /* Per-iteration record of the last scf_run: up to max_rows rows of 6 doubles
  * (iteration, energy, energy change, max|X^T(FDS - SDF)X|, exchange slices (0 = FP64), J/K build ms).

@@ -23,8 +23,11 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_mlp_free", "df_mlp_nparams", "df_mlp_params", "df_mlp_gradients", "df_mlp_train", "df_mlp_predict",
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
             "df_fp64_rate", "df_sad_density", "df_build_B_batch",
-            "df_init_open", "scf_run_uhf", "scf_run_rohf"]
+            "df_init_open", "scf_run_uhf", "scf_run_rohf", "df_water_pairs", "df_pair_blocks", "df_pair_density",
+            "df_mlp_guess_pairs"]
 DF_MLP_NFEAT = 57
+DF_MLP_NPFEAT = 26
+PAIR_CUTOFF = 7.5      # bohr, O-O distance of the water pairs whose blocks the pair network predicts
 
 
 class Atom(ctypes.Structure):
@@ -109,6 +112,11 @@ def load(path: str | None = None):
     L.df_water_blocks.argtypes = [c_void_p, dp, fp]
     L.df_water_density.argtypes = [c_void_p, fp, dp]
     L.df_mlp_guess.argtypes = [c_void_p, c_void_p, c_int, dp]
+    ip = P(c_int)
+    L.df_water_pairs.argtypes = [P(Atom), c_int, ctypes.c_double, ip, c_int, fp]
+    L.df_pair_blocks.argtypes = [c_void_p, dp, ip, c_int, fp]
+    L.df_pair_density.argtypes = [c_void_p, fp, ip, c_int, dp]
+    L.df_mlp_guess_pairs.argtypes = [c_void_p, c_void_p, c_void_p, ctypes.c_double, c_int, dp]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -236,9 +244,32 @@ class Handle:
         self._check(load().df_water_density(self.h, _fp(blocks), _dp(D0)), "df_water_density")
         return D0
 
-    def mlp_guess(self, mlp, bf16=True):
+    def mlp_guess(self, mlp, bf16=True, pair_mlp=None, cutoff=PAIR_CUTOFF):
+        """Learned D0: diagonal water blocks from `mlp`, plus (if given) the blocks of the water pairs within
+        `cutoff` bohr from `pair_mlp` (df_mlp_guess_pairs)."""
         D0 = np.empty((self.n, self.n))
-        self._check(load().df_mlp_guess(self.h, mlp.m, int(bf16), _dp(D0)), "df_mlp_guess")
+        if pair_mlp is None:
+            self._check(load().df_mlp_guess(self.h, mlp.m, int(bf16), _dp(D0)), "df_mlp_guess")
+        else:
+            self._check(load().df_mlp_guess_pairs(self.h, mlp.m, pair_mlp.m, float(cutoff), int(bf16), _dp(D0)),
+                        "df_mlp_guess_pairs")
+        return D0
+
+    def pair_blocks(self, D, pairs):
+        """Frame blocks (npairs x nb x nb, float32) of the ordered water pairs `pairs` (npairs x 2) of D."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        nbw = water_nbf(self.system)
+        out = np.empty((len(pairs), nbw, nbw), dtype=np.float32)
+        self._check(load().df_pair_blocks(self.h, _dp(D), _ip(pairs), len(pairs), _fp(out)), "df_pair_blocks")
+        return out
+
+    def pair_density(self, blocks, pairs, D0=None):
+        """D0 (zero if not given) plus the laboratory-frame pair blocks (df_pair_density)."""
+        blocks = np.ascontiguousarray(blocks, dtype=np.float32)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        D0 = np.zeros((self.n, self.n)) if D0 is None else np.ascontiguousarray(D0, dtype=np.float64).copy()
+        self._check(load().df_pair_density(self.h, _fp(blocks), _ip(pairs), len(pairs), _dp(D0)), "df_pair_density")
         return D0
 
     def scf_uhf(self, nalpha, nbeta, conv_E=1e-10, conv_err=1e-7, max_iter=200, diis_size=8, precision=DF_PREC_FP64,
@@ -354,6 +385,10 @@ def _fp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
 def water_nbf(system) -> int:
     return int((2 * system.basis["l"][system.basis["atom"] < 3] + 1).sum())
 
@@ -366,6 +401,22 @@ def water_features(system):
     if rc < 0:
         raise DFError(rc, "df_water_features")
     return out
+
+
+def water_pairs(system, cutoff=PAIR_CUTOFF):
+    """Ordered water pairs within `cutoff` bohr (O-O), both orders: (pairs int32 (k, 2), features float32
+    (k, DF_MLP_NPFEAT))."""
+    atoms = _atoms(system.atoms)
+    n = load().df_water_pairs(atoms, len(system.atoms), float(cutoff), None, 0, None)
+    if n < 0:
+        raise DFError(n, "df_water_pairs")
+    pairs = np.zeros((n, 2), dtype=np.int32)
+    feats = np.zeros((n, DF_MLP_NPFEAT), dtype=np.float32)
+    if n:
+        rc = load().df_water_pairs(atoms, len(system.atoms), float(cutoff), _ip(pairs), n, _fp(feats))
+        if rc < 0:
+            raise DFError(rc, "df_water_pairs")
+    return pairs, feats
 
 
 class Mlp:

@@ -1,7 +1,10 @@
 // Learned initial guess: a small MLP maps rotation-invariant features of each water's environment to
 // the water's 50 x 50 diagonal density block expressed in the molecule's own frame; the blocks are
 // rotated to the laboratory frame with real-solid-harmonic rotation matrices (l <= 2) and assembled
-// block-diagonally into D0. The SCF then starts from the natural orbitals of D0 (scf_run_guess).
+// block-diagonally into D0. A second network maps features of each ordered pair of waters within a cutoff
+// (the second water's atoms in the first one's frame, atom-pair distances) to the pair's 50 x 50
+// off-diagonal block in the first water's frame. The SCF then starts from the natural orbitals of D0
+// (scf_run_guess).
 // Training (forward, backward, Adam) and BF16 inference run in this file's CUDA kernels.
 // The paper has no learned guess; this is the build's design (its quality is a measured outcome).
 #include <cuda_bf16.h>
@@ -396,6 +399,60 @@ void water_features(const df_atom* atoms, int natom, const std::vector<Frame>& f
     }
 }
 
+// pair features of the ordered water pair (w1, w2) (DF_MLP_NPFEAT values): the atoms of w2 in w1's frame
+// relative to w1's O (divided by 10 bohr), 5 bohr / r for the nine atom pairs between the two waters, and
+// a Gaussian expansion of the O-O distance (8 centres 4.5 + 0.5 k bohr, width 0.35 bohr)
+constexpr int NPFEAT = 26;
+void pair_features(const df_atom* atoms, const std::vector<Frame>& fr, int w1, int w2, float* out) {
+    auto dist = [&](int a, int b) {
+        double r2 = 0;
+        for (int d = 0; d < 3; ++d) r2 += (atoms[a].xyz[d] - atoms[b].xyz[d]) * (atoms[a].xyz[d] - atoms[b].xyz[d]);
+        return std::sqrt(r2);
+    };
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            double v = 0;
+            for (int d = 0; d < 3; ++d) v += fr[w1].R[d][c] * (atoms[3 * w2 + a].xyz[d] - fr[w1].O[d]);
+            out[3 * a + c] = (float)(v / 10.0);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out[9 + 3 * a + b] = (float)(5.0 / dist(3 * w1 + a, 3 * w2 + b));
+    const double r = dist(3 * w1, 3 * w2);
+    for (int k = 0; k < 8; ++k) {
+        const double c = 4.5 + 0.5 * k;
+        out[18 + k] = (float)std::exp(-(r - c) * (r - c) / (2 * 0.35 * 0.35));
+    }
+}
+
+// ordered pairs (w1 != w2) with O-O distance <= cutoff, by w1 then w2
+std::vector<std::pair<int, int>> water_pair_list(const df_atom* atoms, int natom, double cutoff) {
+    std::vector<std::pair<int, int>> out;
+    const int nw = natom / 3;
+    for (int w1 = 0; w1 < nw; ++w1)
+        for (int w2 = 0; w2 < nw; ++w2) {
+            if (w1 == w2) continue;
+            double r2 = 0;
+            for (int d = 0; d < 3; ++d) {
+                const double x = atoms[3 * w1].xyz[d] - atoms[3 * w2].xyz[d];
+                r2 += x * x;
+            }
+            if (r2 <= cutoff * cutoff) out.push_back({w1, w2});
+        }
+    return out;
+}
+
+// C = A B (nb x nb, row-major); tA / tB use the transposes
+void small_mm(const std::vector<double>& A, bool tA, const std::vector<double>& B, bool tB, int nb,
+              std::vector<double>& C) {
+    C.assign((size_t)nb * nb, 0.0);
+    for (int i = 0; i < nb; ++i)
+        for (int k = 0; k < nb; ++k) {
+            const double a = tA ? A[(size_t)k * nb + i] : A[(size_t)i * nb + k];
+            if (a == 0.0) continue;
+            for (int j = 0; j < nb; ++j) C[(size_t)i * nb + j] += a * (tB ? B[(size_t)j * nb + k] : B[(size_t)k * nb + j]);
+        }
+}
+
 }  // namespace
 }  // namespace dfhf
 
@@ -670,6 +727,108 @@ int df_mlp_guess(df_handle* h, df_mlp* m, int bf16, double* D0) {
     rc = df_mlp_predict(m, X.data(), nw, bf16, Y.data());
     if (rc != DF_OK) return rc;
     return df_water_density(h, Y.data(), D0);
+}
+
+int df_water_pairs(const df_atom* atoms, int natom, double cutoff, int* pairs, int max_pairs, float* feats) {
+    if (!atoms || natom < 3 || !(cutoff > 0) || max_pairs < 0 || (max_pairs > 0 && !pairs)) return DF_E_ARG;
+    try {
+        const std::vector<Frame> fr = water_frames(atoms, natom);
+        const auto list = water_pair_list(atoms, natom, cutoff);
+        for (int k = 0; k < (int)list.size() && k < max_pairs; ++k) {
+            pairs[2 * k] = list[k].first;
+            pairs[2 * k + 1] = list[k].second;
+            if (feats) pair_features(atoms, fr, list[k].first, list[k].second, feats + (size_t)k * NPFEAT);
+        }
+        return (int)list.size();
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+// out[k] = M_1 D[w1][w2] M_2^T (nb x nb, row-major): the block of the ordered pair in w1's frame (M_2 rotates
+// w2's functions by w1's frame)
+int df_pair_blocks(df_handle* h, const double* D, const int* pairs, int npairs, float* out) {
+    if (!h || !D || npairs < 0 || (npairs > 0 && (!pairs || !out))) return DF_E_ARG;
+    try {
+        const std::vector<Frame> fr = water_frames(h->atoms.data(), (int)h->atoms.size());
+        const int nbw = water_nbf(h), nw = (int)fr.size();
+        std::vector<double> M1, M2, Dl((size_t)nbw * nbw), T1, T;
+        for (int k = 0; k < npairs; ++k) {
+            const int w1 = pairs[2 * k], w2 = pairs[2 * k + 1];
+            if (w1 < 0 || w2 < 0 || w1 >= nw || w2 >= nw || w1 == w2) throw Error{DF_E_ARG, "df_pair_blocks: bad pair"};
+            int f1 = 0, f2 = 0;
+            water_rotation(h, w1, fr[w1], nbw, M1, f1);
+            water_rotation(h, w2, fr[w1], nbw, M2, f2);
+            for (int a = 0; a < nbw; ++a)
+                for (int b = 0; b < nbw; ++b) Dl[(size_t)a * nbw + b] = D[(size_t)(f1 + a) * h->n + f2 + b];
+            small_mm(M1, false, Dl, false, nbw, T1);
+            small_mm(T1, false, M2, true, nbw, T);
+            for (size_t i = 0; i < T.size(); ++i) out[(size_t)k * nbw * nbw + i] = (float)T[i];
+        }
+    } catch (const Error& e) {
+        return fail_code(h, e);
+    }
+    return DF_OK;
+}
+
+// D0 += the laboratory-frame pair blocks M_1^T T M_2 at [w1][w2] and their transposes at [w2][w1]; a pair
+// listed in both orders contributes the mean of its two blocks
+int df_pair_density(df_handle* h, const float* blocks, const int* pairs, int npairs, double* D0) {
+    if (!h || !D0 || npairs < 0 || (npairs > 0 && (!pairs || !blocks))) return DF_E_ARG;
+    try {
+        const std::vector<Frame> fr = water_frames(h->atoms.data(), (int)h->atoms.size());
+        const int nbw = water_nbf(h), nw = (int)fr.size();
+        std::vector<int> count((size_t)nw * nw, 0);
+        for (int k = 0; k < npairs; ++k) {
+            const int w1 = pairs[2 * k], w2 = pairs[2 * k + 1];
+            if (w1 < 0 || w2 < 0 || w1 >= nw || w2 >= nw || w1 == w2) throw Error{DF_E_ARG, "df_pair_density: bad pair"};
+            ++count[(size_t)std::min(w1, w2) * nw + std::max(w1, w2)];
+        }
+        std::vector<double> M1, M2, T((size_t)nbw * nbw), T1, L;
+        for (int k = 0; k < npairs; ++k) {
+            const int w1 = pairs[2 * k], w2 = pairs[2 * k + 1];
+            const double wgt = 1.0 / count[(size_t)std::min(w1, w2) * nw + std::max(w1, w2)];
+            int f1 = 0, f2 = 0;
+            water_rotation(h, w1, fr[w1], nbw, M1, f1);
+            water_rotation(h, w2, fr[w1], nbw, M2, f2);
+            for (size_t i = 0; i < T.size(); ++i) T[i] = blocks[(size_t)k * nbw * nbw + i];
+            small_mm(M1, true, T, false, nbw, T1);
+            small_mm(T1, false, M2, false, nbw, L);
+            for (int a = 0; a < nbw; ++a)
+                for (int b = 0; b < nbw; ++b) {
+                    const double v = wgt * L[(size_t)a * nbw + b];
+                    D0[(size_t)(f1 + a) * h->n + f2 + b] += v;
+                    D0[(size_t)(f2 + b) * h->n + f1 + a] += v;
+                }
+        }
+    } catch (const Error& e) {
+        return fail_code(h, e);
+    }
+    return DF_OK;
+}
+
+// learned D0 with pair blocks: the diagonal blocks from m (df_mlp_guess) plus the blocks of every water pair
+// within `cutoff` bohr (O-O) from mp, in both orders
+int df_mlp_guess_pairs(df_handle* h, df_mlp* m, df_mlp* mp, double cutoff, int bf16, double* D0) {
+    if (!h || !m || !mp || !D0 || !(cutoff > 0)) return DF_E_ARG;
+    const int nbw = water_nbf(h);
+    if (mp->nin != NPFEAT || mp->nout != nbw * nbw) {
+        h->last_error = "df_mlp_guess_pairs: pair network shape does not match the pair features / water basis";
+        return DF_E_ARG;
+    }
+    int rc = df_mlp_guess(h, m, bf16, D0);
+    if (rc != DF_OK) return rc;
+    const int natom = (int)h->atoms.size();
+    const int np = df_water_pairs(h->atoms.data(), natom, cutoff, nullptr, 0, nullptr);
+    if (np < 0) return np;
+    if (np == 0) return DF_OK;
+    std::vector<int> pairs(2 * (size_t)np);
+    std::vector<float> X((size_t)np * NPFEAT), Y((size_t)np * mp->nout);
+    rc = df_water_pairs(h->atoms.data(), natom, cutoff, pairs.data(), np, X.data());
+    if (rc < 0) return rc;
+    rc = df_mlp_predict(mp, X.data(), np, bf16, Y.data());
+    if (rc != DF_OK) return rc;
+    return df_pair_density(h, Y.data(), pairs.data(), np, D0);
 }
 
 // D0 (host n x n) from reference-frame blocks (nwater x ntri): block-diagonal M^T T_w M
