@@ -210,6 +210,8 @@ void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* 
 // split precision (split_k.cu)
 void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double* dK);
 void split_clear_error(df_handle* h);
+// the split exchange's Y buffer viewed as doubles, if it holds at least `elems` of them (else nullptr)
+double* split_y_buffer(df_handle* h, long long elems);
 void free_split(df_handle* h);
 
 // static scratch of df_coulomb_noalloc (coulomb_noalloc.cu): device address of the array on the current

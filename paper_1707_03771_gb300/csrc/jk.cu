@@ -175,12 +175,18 @@ void exchange_fp64(df_handle* h, int nocc, double* dK) {
     PhaseTimer t(h->sync_timing, 3);
     t.mark(0, s);
     h->exchange_launches = 3;   // Y transform, K contraction, K reduction
-    const size_t ny = (size_t)h->naux * pk.np * ldy;   // the FP64 Y is allocated on first FP64 use only
-    if (h->Y.n < ny) h->Y.alloc(ny);
-    y_transform_fp64(s, h->B.p, pk.row, pk.nt, h->naux, h->Cpad.p, ldy, nocc, h->Y.p);
+    // Y (naux x np x ldy doubles): the split exchange's Y buffer when the handle has one large enough (8 bytes
+    // per element as well; both run in order on the handle's stream), else its own, allocated on first use
+    const size_t ny = (size_t)h->naux * pk.np * ldy;
+    double* Y = split_y_buffer(h, (long long)ny);
+    if (!Y) {
+        if (h->Y.n < ny) h->Y.alloc(ny);
+        Y = h->Y.p;
+    }
+    y_transform_fp64(s, h->B.p, pk.row, pk.nt, h->naux, h->Cpad.p, ldy, nocc, Y);
     t.mark(1, s);
     const int ntiles = pk.nt * (pk.nt + 1) / 2;
-    k_syrk_fp64(s, h->Y.p, h->naux, pk.np, ldy, nocc, k_splits(h), h->ktiles.p, ntiles, h->Kpart.p, h->n, dK);
+    k_syrk_fp64(s, Y, h->naux, pk.np, ldy, nocc, k_splits(h), h->ktiles.p, ntiles, h->Kpart.p, h->n, dK);
     t.mark(2, s);
     if (t.on) {
         t.sync(2);

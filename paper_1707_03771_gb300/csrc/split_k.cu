@@ -155,6 +155,49 @@ __global__ void __launch_bounds__(256) split_b_tiles_kernel(const double* __rest
         }
 }
 
+// pmax[P] = max |B_P| as the bit pattern of a non-negative double, tile by tile
+__global__ void __launch_bounds__(256) p_max_tiles_kernel(const double* __restrict__ B, long long row,
+                                                          unsigned long long* __restrict__ pmax) {
+    const long long tp = blockIdx.x, P = blockIdx.y;
+    const double* src = B + P * row + tp * 4096;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < 4096; i += 256) m = fmax(m, fabs(src[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(pmax + P, (unsigned long long)__double_as_longlong(m));
+}
+
+// slices of rows [0, nrows) of B into the packed layout Bs[s][P][t][128][128] (lower 128-tiles
+// t = I (I + 1) / 2 + J, I >= J), one exponent Be[P] per row: the packed 64-tile (i, j) is block
+// (i % 2, j % 2) of 128-tile (i / 2, j / 2); inside a diagonal 128-tile the off-diagonal 64-tile is also
+// written transposed, so that diagonal tiles are whole. Blocks no 64-tile reaches (padding) stay as set
+// at allocation (zero).
+template <int S>
+__global__ void __launch_bounds__(256) split_b_packed_kernel(const double* __restrict__ B, long long row,
+                                                             const int* __restrict__ Be, long long ntile,
+                                                             bf16* __restrict__ Bs, long long sstride) {
+    __shared__ double tile[64][65];
+    const long long tp = blockIdx.x, P = blockIdx.y;
+    int I, J;
+    tile_of(tp, I, J);
+    const double* src = B + P * row + tp * 4096;
+    for (int i = threadIdx.x; i < 4096; i += 256) tile[i >> 6][i & 63] = src[i];
+    __syncthreads();
+    const int e = Be[P];
+    const int IB = I >> 1, JB = J >> 1;
+    bf16* out = Bs + (P * ntile + (long long)IB * (IB + 1) / 2 + JB) * 16384;
+    const int ro = (I & 1) * 64, co = (J & 1) * 64;
+    for (int i = threadIdx.x; i < 4096; i += 256) {
+        const int r = i >> 6, c = i & 63;
+        split_pow2<S>(tile[r][c], e, out + (ro + r) * 128 + co + c, sstride);
+    }
+    if (IB == JB && I != J)
+        for (int i = threadIdx.x; i < 4096; i += 256) {
+            const int r = i & 63, c = i >> 6;
+            split_pow2<S>(tile[r][c], e, out + (co + c) * 128 + ro + r, sstride);
+        }
+}
+
 // C (n x nocc row-major) -> Cs[s][i][nu] (ldy x np), exponent per column i
 template <int S>
 __global__ void __launch_bounds__(256) split_c_kernel(const double* __restrict__ C, int n, int nocc, int np, int ldy,
@@ -552,10 +595,18 @@ bool use_tensor_cores() {
     return !(v && v[0] == '0');
 }
 
+// the tensor-core Y reads B's slices as packed lower 128-tiles (DFHF_TC_PACKED=1) or as full rows
+bool use_packed_slices() {
+    const char* v = std::getenv("DFHF_TC_PACKED");
+    return v && v[0] == '1';
+}
+
 }  // namespace
 
 void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce, int naux,
                 int np, int ldy, float2* Y, int* err);
+void y_split_tc_packed(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce,
+                       int naux, int zrows, int np, int nB, int ldy, float2* Y, int* err);
 void k_split_tc(cudaStream_t s, int S, int N, const bf16* Ys, const int* Ye, int naux, int np, int ldy, int nsplit,
                 const int2* tiles128, int ntiles, float2* Kpart, int npt, int* err);
 void k_tc_reduce(cudaStream_t s, const float2* Kpart, int nsplit, int npt, int n, double* K);
@@ -587,6 +638,12 @@ struct SplitState {
     int PB = 0;
     bool blocked = false;        // B slices cut per block of pblk auxiliary rows at every build
     int pblk = 0;
+    // B slice layout: tensor-core path packed lower 128-tiles with one exponent per auxiliary row
+    // (Bs [S][rows][nB (nB + 1) / 2][128][128], Be [naux]); mma.sync path full rows with one exponent per
+    // (P, mu) (Bs [S][rows][np][np], Be [naux][np])
+    bool packed = false;
+    int nB = 0;
+    long long ntile = 0;
     // tile choice per slice count, fixed at this state's first build with that count (0: not yet):
     // Y tile width, K tile width, K split; buffers sized for it are never reallocated under queued work
     int ch_y[SMAX + 1] = {0}, ch_k[SMAX + 1] = {0}, ch_split[SMAX + 1] = {0};
@@ -628,21 +685,52 @@ void row_exponents(df_handle* h, SplitState* st) {
     DF_CUDA(cudaStreamSynchronize(h->stream));   // rmax is released on return
 }
 
-// slices of auxiliary rows [p0, p0 + nb) into Bs (block-local rows)
+// one exponent per auxiliary row P (packed layout): max over B_P
+void p_exponents(df_handle* h, SplitState* st) {
+    if (h->naux > 65535) throw Error{DF_E_ARG, "split exchange supports at most 65535 auxiliary functions"};
+    DF_CUDA(cudaMalloc((void**)&st->Be, sizeof(int) * h->naux));
+    DevBuf<unsigned long long> pmax;
+    pmax.alloc(h->naux);
+    pmax.zero(h->stream);
+    p_max_tiles_kernel<<<dim3((unsigned)h->pk.ntp, h->naux), 256, 0, h->stream>>>(h->B.p, h->pk.row, pmax.p);
+    DF_CHECK_LAUNCH();
+    row_exponent_kernel<<<nblocks(h->naux, 256), 256, 0, h->stream>>>(pmax.p, h->naux, st->Be);
+    DF_CHECK_LAUNCH();
+    DF_CUDA(cudaStreamSynchronize(h->stream));   // pmax is released on return
+}
+
+// elements of one auxiliary row's slices in the state's layout
+long long row_elems(const SplitState* st) { return st->packed ? st->ntile * 16384 : (long long)st->np * st->np; }
+
+// the slice buffer for `rows` auxiliary rows (zeroed: the packed layout's padding is never written)
+void alloc_b_slices(df_handle* h, SplitState* st, long long rows) {
+    const long long elems = (long long)SMAX * rows * row_elems(st);
+    DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * elems));
+    if (st->packed) DF_CUDA(cudaMemsetAsync(st->Bs, 0, sizeof(bf16) * elems, h->stream));
+}
+
+void b_exponents(df_handle* h, SplitState* st) {
+    if (st->packed) p_exponents(h, st);
+    else row_exponents(h, st);
+}
+
+// slices of auxiliary rows [p0, p0 + nb) into Bs (block-local rows; bstr = elements per slice)
 template <int S>
 void slice_b_rows(df_handle* h, SplitState* st, int p0, int nb, long long bstr) {
-    split_b_tiles_kernel<S><<<dim3((unsigned)h->pk.ntp, nb), 256, 0, h->stream>>>(
-        h->B.p + (long long)p0 * h->pk.row, h->pk.row, st->np, st->Be + (long long)p0 * st->np, st->Bs, bstr);
+    if (st->packed)
+        split_b_packed_kernel<S><<<dim3((unsigned)h->pk.ntp, nb), 256, 0, h->stream>>>(
+            h->B.p + (long long)p0 * h->pk.row, h->pk.row, st->Be + p0, st->ntile, st->Bs, bstr);
+    else
+        split_b_tiles_kernel<S><<<dim3((unsigned)h->pk.ntp, nb), 256, 0, h->stream>>>(
+            h->B.p + (long long)p0 * h->pk.row, h->pk.row, st->np, st->Be + (long long)p0 * st->np, st->Bs, bstr);
     DF_CHECK_LAUNCH();
 }
 
 template <int S>
 void prepare_b(df_handle* h, SplitState* st) {
-    const long long np = st->np;
-    const long long bstr = (long long)h->naux * np * np;
-    DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * S * bstr));
-    row_exponents(h, st);
-    slice_b_rows<S>(h, st, 0, h->naux, bstr);
+    alloc_b_slices(h, st, h->naux);
+    b_exponents(h, st);
+    slice_b_rows<S>(h, st, 0, h->naux, (long long)h->naux * row_elems(st));
 }
 
 // ---- autotuner ----------------------------------------------------------------------------------
@@ -674,15 +762,23 @@ double time_once(cudaStream_t s, F&& launch) {
     return ms;
 }
 
+// tensor-core Y of auxiliary rows [p0, p0 + nb) held in the slice buffer (block-local rows)
+void y_tc(df_handle* h, SplitState* st, int S, int N, int p0, int nb, float2* Yb) {
+    if (st->packed)   // slices at the buffer's full row stride (the padding of every block stays zero)
+        y_split_tc_packed(h->stream, S, N, st->Bs, st->Be + p0, st->Cs, st->Ce, nb, st->blocked ? st->pblk : h->naux,
+                          st->np, st->nB, st->ldy, Yb, st->err);
+    else
+        y_split_tc(h->stream, S, N, st->Bs, st->Be + (long long)p0 * st->np, st->Cs, st->Ce, nb, st->np, st->ldy, Yb,
+                   st->err);
+}
+
 template <int S>
 int tune_y(df_handle* h, SplitState* st, int nb, float2* Yb) {
     double best_ms = 1e30;
     int best = 0;
     for (int N : {80, 64, 32}) {
         if (st->ldy % N) continue;
-        const double ms = time_once(h->stream, [&] {
-            y_split_tc(h->stream, S, N, st->Bs, st->Be, st->Cs, st->Ce, nb, st->np, st->ldy, Yb, st->err);
-        });
+        const double ms = time_once(h->stream, [&] { y_tc(h, st, S, N, 0, nb, Yb); });
         if (ms < best_ms) {
             best_ms = ms;
             best = N;
@@ -737,6 +833,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const size_t smem = (size_t)2 * S * (64 + BN) * LDS * sizeof(bf16) + (64 + BN) * sizeof(int);
     DF_CUDA(cudaFuncSetAttribute(y_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const bool tc = use_tensor_cores() && (S == 3 || S == 5);
+    if (st->packed && !tc) throw Error{DF_E_ARG, "internal: B slice layout does not match the exchange kernels"};
     const std::array<int, 4> key{np, ldy, (naux + 511) / 512, S};
     TcChoice ch;
     bool have = !tc;
@@ -767,9 +864,11 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
     const int pblk = st->blocked ? st->pblk : naux;
     for (int p0 = 0; p0 < naux; p0 += pblk) {
         const int nb = std::min(pblk, naux - p0);
-        const long long bstr = (long long)(st->blocked ? nb : naux) * np * np;
+        // slice stride: the packed layout keeps the buffer's full row count, so that the zero padding of
+        // the last 128-tiles sits at the same place for every block
+        const long long bstr = (long long)(st->blocked ? (st->packed ? st->pblk : nb) : naux) * row_elems(st);
         if (st->blocked) slice_b_rows<S>(h, st, p0, nb, bstr);
-        const int* Beb = st->Be + (long long)p0 * np;   // row exponents of the block
+        const int* Beb = st->Be + (long long)p0 * np;   // row exponents of the block (mma.sync layout)
         float2* Yb = st->Y + (long long)p0 * np * ldy;
         if (tc) {
             if (!have && p0 == 0) {
@@ -777,7 +876,7 @@ void run_split(df_handle* h, SplitState* st, const double* dC, int nocc, double*
                 ch.yN = tune_y<S>(h, st, nb, Yb);
                 tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             }
-            y_split_tc(s, S, ch.yN, st->Bs, Beb, st->Cs, st->Ce, nb, np, ldy, Yb, st->err);
+            y_tc(h, st, S, ch.yN, p0, nb, Yb);
         } else {
             y_split_kernel<S><<<dim3(np / 64, nb, (ldy + BN - 1) / BN), 64 * WN, smem, s>>>(st->Bs, bstr, Beb, st->Cs,
                                                                                            cstr, st->Ce, np, ldy, Yb);
@@ -868,7 +967,10 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     if (slices < 2 || slices > SMAX) throw Error{DF_E_ARG, "slices must be 2..5"};
     if (h->pk.np % 64) throw Error{DF_E_ARG, "internal: padded size not a multiple of 64"};
     SplitState* st = h->split;
-    if (st && st->S < slices) {
+    // the tensor-core kernels read the packed slice layout, the mma.sync kernels the full one: a build of the
+    // other kind re-cuts the slices (tests switch kernels on one handle; an SCF stays with one kind)
+    const bool want_packed = use_tensor_cores() && use_packed_slices() && (slices == 3 || slices == 5);
+    if (st && (st->S < slices || st->packed != want_packed)) {
         free_split(h);
         st = nullptr;
     }
@@ -882,15 +984,23 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         st = new SplitState();
         h->split = st;
         st->np = h->pk.np;
+        st->packed = want_packed;
+        st->nB = (st->np + 127) / 128;
+        st->ntile = (long long)st->nB * (st->nB + 1) / 2;
         const long long np = st->np;
+        // FP64 builds on this handle borrow the split Y from now on: an FP64 Y already allocated goes
+        if (h->Y.p) {
+            DF_CUDA(cudaStreamSynchronize(h->stream));
+            h->Y.release();
+        }
         size_t free_b = 0, total_b = 0;
         DF_CUDA(cudaMemGetInfo(&free_b, &total_b));
         // SMAX slices of every auxiliary row when they fit beside Y and its slices; otherwise SMAX slices
         // of blocks of rows, cut from B at each build
-        const double row_slices = 2.0 * SMAX * np * np;                      // one row, every slice
+        const double row_slices = 2.0 * SMAX * row_elems(st);                // one row, every slice
         const double ybytes = (8.0 + 2.0 * SMAX) * h->naux * np * ldy;      // Y and its slices
-        // kept free: an FP64 Y of the same shape (FP64 builds on the same handle) and working space
-        const double slack = 8.0 * h->naux * np * ldy + 16.0 * np * np + (4ull << 30);
+        // kept free: working space (FP64 builds on the same handle use the split Y buffer)
+        const double slack = 16.0 * np * np + (4ull << 30);
         st->S = SMAX;
         // DFHF_SPLIT_BLOCK_ROWS=r forces blocks of r rows (tests compare the two modes)
         const char* fb = std::getenv("DFHF_SPLIT_BLOCK_ROWS");
@@ -898,8 +1008,8 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         if (forced > 0) {
             st->blocked = true;
             st->pblk = std::min(forced, h->naux);
-            DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
-            row_exponents(h, st);
+            alloc_b_slices(h, st, st->pblk);
+            b_exponents(h, st);
         } else if ((double)free_b > row_slices * h->naux + ybytes + slack) {
             prepare_b<SMAX>(h, st);
         } else {
@@ -907,8 +1017,8 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
             if (avail < row_slices) throw Error{DF_E_NOMEM, "split exchange: no room for one row of B slices"};
             st->blocked = true;
             st->pblk = (int)std::min<double>(h->naux, std::floor(avail / row_slices));
-            DF_CUDA(cudaMalloc((void**)&st->Bs, sizeof(bf16) * SMAX * (long long)st->pblk * np * np));
-            row_exponents(h, st);
+            alloc_b_slices(h, st, st->pblk);
+            b_exponents(h, st);
         }
     }
     if (ldy != st->ldy) {
@@ -1011,6 +1121,12 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         h->timings_ms[10] = ev.ms(3, 4);   // K contraction (split)
         h->timings_ms[11] = h->timings_ms[8] - h->timings_ms[9] - h->timings_ms[10];   // slicing, reduce
     }
+}
+
+double* split_y_buffer(df_handle* h, long long elems) {
+    const SplitState* st = h->split;
+    if (!st || !st->Y || (long long)h->naux * st->np * st->ldy_cap < elems) return nullptr;
+    return reinterpret_cast<double*>(st->Y);
 }
 
 void split_clear_error(df_handle* h) {

@@ -95,6 +95,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// MN-major operand (the M index contiguous in shared memory, 128-byte swizzle): the tile is two 8 KB halves
+// of 64 M-values each (one per TMA box), each half 8 K-rows of 128 bytes per 1024-byte atom. One stride
+// field steps between the halves (along M), the other between 8-row atoms (along K).
+constexpr unsigned MN_LBO = 8192;   // bytes between the two 64-wide M halves
+constexpr unsigned MN_SBO = 1024;   // bytes between 8-row atoms along K
+__device__ __forceinline__ uint64_t smem_desc_mn(const void* tile) {
+    const unsigned a = smem_u32(tile);
+    uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+    d |= (uint64_t)(MN_LBO >> 4) << 16;
+    d |= (uint64_t)(MN_SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart
 __device__ __forceinline__ uint64_t smem_desc(const void* tile) {
     const unsigned a = smem_u32(tile);
@@ -149,7 +164,10 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 // ------------------------------------------------------------------------------------------------
 // Work description. MODE 0 (Y = B C): CTA = (P, mu-tile, n-tile); K runs over nu (np), exponents
-// constant (row: Be[P][mu], column: Ce[i]). MODE 1 (K = sum Y Y^T): CTA = (split, lower tile pair,
+// constant (row: Be[P][mu], column: Ce[i]). MODE 3 (Y = B C from the packed slices): B_P is stored as its
+// lower 128 x 128 tiles only, Bs[s][P][t][128][128] with t = I (I + 1) / 2 + J for I >= J (diagonal tiles
+// whole), one exponent per P (Be[P]); K-step blocks nu of J > I come from the stored tile (J, I) read as an
+// MN-major (transposed) operand. MODE 1 (K = sum Y Y^T): CTA = (split, lower tile pair,
 // column part), the split slowest so that the CTAs resident together stream the same range of the
 // contraction through L2; K runs over the contiguous index k = P ldy + i of the Y slices, stored tile-major
 // as Ys[s][k / 64][mu][k % 64] (one TMA box is 16 KB of contiguous memory; no padding between auxiliary
@@ -173,6 +191,7 @@ struct TcArgs {
     double* outd;
     long long ldo;
     long long wait_cycles;   // budget of the pipeline waits (WAIT_CYCLES by default)
+    int nB;                  // MODE 3: 128-row blocks of the packed tiles (np padded to 128 nB)
 };
 
 template <int S, int N, int MODE>
@@ -208,8 +227,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
     int2 IJ = make_int2(0, 0);
     int ksteps = 0;
     int p0 = 0, kpp = 0;   // MODE 1: first chunk and first K-step of the split
-    if (MODE == 0) {
-        const int mt = (args.np + TM - 1) / TM;
+    if (MODE == 0 || MODE == 3) {
+        const int mt = MODE == 3 ? args.nB : (args.np + TM - 1) / TM;
         const int nt = args.ldy / N;
         int b = blockIdx.x;
         const int ntile = b % nt;
@@ -217,7 +236,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
         m0 = (b % mt) * TM;
         P = b / mt;
         n0 = ntile * N;
-        ksteps = args.np / KS;
+        ksteps = MODE == 3 ? 2 * args.nB : args.np / KS;
     } else if (MODE == 2) {
         const int ntn = args.ncols / N;
         m0 = (blockIdx.x / ntn) * TM;             // row-tile major: the L^-1 tile is shared in L2
@@ -296,8 +315,24 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                         break;
                     }
                     mbar_expect_tx(&a_full[slot], A_BYTES);
-                    const int za = MODE == 0 ? s * args.naux + P : (MODE == 1 ? s * args.nkb + kb : s);
-                    tma_load_3d(smem + slot * A_BYTES, &mapA, kx, m0, za, &a_full[slot]);
+                    const int za = (MODE == 0 || MODE == 3) ? s * args.naux + P : (MODE == 1 ? s * args.nkb + kb : s);
+                    if (MODE == 3) {
+                        // two 64-row boxes of one stored tile: rows mu of tile (I, J) at columns nu of this
+                        // K-step (K-major), or, above the diagonal, rows nu of tile (J, I) (MN-major halves)
+                        const int I = m0 / TM, J = ks >> 1, half = ks & 1;
+                        unsigned char* dst = smem + slot * A_BYTES;
+                        if (I >= J) {
+                            const int y0 = (I * (I + 1) / 2 + J) * TM;
+                            tma_load_3d(dst, &mapA, half * KS, y0, za, &a_full[slot]);
+                            tma_load_3d(dst + A_BYTES / 2, &mapA, half * KS, y0 + KS, za, &a_full[slot]);
+                        } else {
+                            const int y0 = (J * (J + 1) / 2 + I) * TM + half * KS;
+                            tma_load_3d(dst, &mapA, 0, y0, za, &a_full[slot]);
+                            tma_load_3d(dst + A_BYTES / 2, &mapA, KS, y0, za, &a_full[slot]);
+                        }
+                    } else {
+                        tma_load_3d(smem + slot * A_BYTES, &mapA, kx, m0, za, &a_full[slot]);
+                    }
                     ++a_issued;
                 }
                 if (!ok) break;
@@ -339,6 +374,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                 fence_after();
                 const bool first_in_chunk = ks == 0 || chunk_of(ks - 1) != c;
                 unsigned char* bset = bbuf + bs * BSET;
+                const bool mn = MODE == 3 && m0 / TM < (ks >> 1);   // A read transposed from the stored tile
+                const unsigned amaj = mn ? (1u << 15) : 0u;
                 for (int s = 0; s < S; ++s) {
                     const int it = ks * S + s, slot = it % NA;
                     if (!mbar_wait(&a_full[slot], (it / NA) & 1, err, wait)) {
@@ -351,11 +388,13 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
                     // MMA of width cnt * N (one read of the A tile per MMA instead of one per slice)
 #pragma unroll
                     for (int k = 0; k < KS / 16; ++k) {
-                        const uint64_t ad = smem_desc(smem + slot * A_BYTES) + (uint64_t)(k * 2);   // +32 B per k16
+                        // K-major: +32 B per k16; MN-major: +2 atoms of 8 K-rows (2048 B) per k16
+                        const uint64_t ad = mn ? smem_desc_mn(smem + slot * A_BYTES + k * 2048)
+                                               : smem_desc(smem + slot * A_BYTES) + (uint64_t)(k * 2);
                         for (int t = 0; t < S - s; t += MMA_SLICES) {
                             const int cnt = min(MMA_SLICES, S - s - t);
                             const uint64_t bd = smem_desc(bset + t * B_BYTES) + (uint64_t)(k * 2);
-                            mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, instr_desc(TM, cnt * N),
+                            mma_bf16(tmem + (unsigned)((s + t) * N), ad, bd, instr_desc(TM, cnt * N) | amaj,
                                      (first_in_chunk && s == 0 && k == 0) ? 0u : 1u);
                         }
                     }
@@ -422,8 +461,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_tc_kernel(const __grid_constant_
 #pragma unroll
                 for (int c = 0; c < N; ++c)
                     o[c] = scale_pow2((double)hi[c] + (double)lo[c], er + __ldg(args.col_e + n0 + c));
-            } else if (MODE == 0) {
-                const int er = args.row_e[(long long)P * args.np + grow];
+            } else if (MODE == 0 || MODE == 3) {
+                const int er = MODE == 3 ? args.row_e[P] : args.row_e[(long long)P * args.np + grow];
                 float2* o = args.out + ((long long)P * args.np + grow) * args.ldy + n0;
 #pragma unroll
                 for (int c = 0; c < N; ++c) {
@@ -557,6 +596,42 @@ void y_split_tc(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, con
     else if (S == 5 && N == 64) y_tc_launch<5, 64>(s, ma, Cs, np, ldy, a, naux);
     else if (S == 3 && N == 32) y_tc_launch<3, 32>(s, ma, Cs, np, ldy, a, naux);
     else if (S == 5 && N == 32) y_tc_launch<5, 32>(s, ma, Cs, np, ldy, a, naux);
+    else throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices and tile widths 32, 64, 80"};
+}
+
+// Y from the packed slices Bs [S][naux][nB (nB + 1) / 2][128][128] (lower 128-tiles, one exponent Be[P]
+// per auxiliary row): tile widths as y_split_tc
+template <int S, int N>
+void y_tc_packed_launch(cudaStream_t s, const CUtensorMap& ma, const bf16* Cs, int np, int ldy, const TcArgs& a,
+                        int naux, int nB) {
+    const CUtensorMap mb = make_map(Cs, np, ldy, S, N);
+    launch_tc<S, N, 3>(s, ma, mb, a, (unsigned)naux * nB * (ldy / N));
+}
+
+// naux rows are computed; the slices of row P sit at z = s * zrows + P (zrows >= naux: the buffer's rows)
+void y_split_tc_packed(cudaStream_t s, int S, int N, const bf16* Bs, const int* Be, const bf16* Cs, const int* Ce,
+                       int naux, int zrows, int np, int nB, int ldy, float2* Y, int* err) {
+    if (ldy % N) throw Error{DF_E_ARG, "tensor-core split Y: tile width must divide the occupied width"};
+    if (np > nB * TM || np % KS) throw Error{DF_E_ARG, "internal: packed tiles do not cover the padded size"};
+    if (zrows < naux) throw Error{DF_E_ARG, "internal: slice buffer smaller than the rows computed"};
+    TcArgs a{};
+    a.mode = 3;
+    a.naux = zrows;
+    a.np = np;
+    a.ldy = ldy;
+    a.nB = nB;
+    a.row_e = Be;
+    a.col_e = Ce;
+    a.out = Y;
+    a.err = err;
+    const unsigned long long ntile = (unsigned long long)nB * (nB + 1) / 2;
+    const CUtensorMap ma = make_map(Bs, TM, ntile * TM, (unsigned long long)S * zrows, KS);
+    if (S == 3 && N == 80) y_tc_packed_launch<3, 80>(s, ma, Cs, np, ldy, a, naux, nB);
+    else if (S == 5 && N == 80) y_tc_packed_launch<5, 80>(s, ma, Cs, np, ldy, a, naux, nB);
+    else if (S == 3 && N == 64) y_tc_packed_launch<3, 64>(s, ma, Cs, np, ldy, a, naux, nB);
+    else if (S == 5 && N == 64) y_tc_packed_launch<5, 64>(s, ma, Cs, np, ldy, a, naux, nB);
+    else if (S == 3 && N == 32) y_tc_packed_launch<3, 32>(s, ma, Cs, np, ldy, a, naux, nB);
+    else if (S == 5 && N == 32) y_tc_packed_launch<5, 32>(s, ma, Cs, np, ldy, a, naux, nB);
     else throw Error{DF_E_ARG, "tensor-core split Y supports 3 or 5 slices and tile widths 32, 64, 80"};
 }
 

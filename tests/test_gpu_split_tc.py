@@ -1,8 +1,10 @@
 """The tcgen05 (TMEM + TMA) split-precision kernels against the mma.sync split kernels and the FP64
-path on the same B and C. The two paths slice B and C identically and form the same exact Y; they
-re-slice Y with exponents over different blocks of the (P, i) contraction (the tensor-core contraction
-over chunks of the contiguous index P ldy + i, the mma.sync one over whole auxiliary rows), so their K
-differ by the splitting error: each is held to the bound 2^(7 - 7S) against FP64, and the two to twice it."""
+path on the same B and C. The tensor-core path cuts B into its lower 128 x 128 tiles with one exponent
+per auxiliary row (the tiles above the diagonal are read transposed), the mma.sync path into full rows
+with one exponent per (P, mu); both cut C the same way. They re-slice Y with exponents over different
+blocks of the (P, i) contraction (the tensor-core contraction over chunks of the contiguous index
+P ldy + i, the mma.sync one over whole auxiliary rows), so their K differ by the splitting error: each is
+held to the bound 2^(7 - 7S) against FP64, and the two to twice it."""
 import os
 
 import numpy as np
