@@ -577,8 +577,9 @@ def learned_guess_net(binding, clusters, n_train):
 
 def guess_study(args):
     """The learned guess on held-out clusters: train on n_train clusters of 4-24 waters (seeds 10000+),
-    evaluate on n_eval clusters of 8-32 waters (seeds 20000+) against the core-Hamiltonian guess, both
-    with the split-precision SCF (incremental Fock late). Prints one JSON line."""
+    evaluate on n_eval clusters of 8-32 waters (seeds 20000+) against the core-Hamiltonian and SAD guesses,
+    with the diagonal and pair networks and with the diagonal network alone, all with the split-precision
+    SCF (incremental Fock late). Prints one JSON line."""
     from paper_1707_03771_gb300 import binding, build, clusters
     build.build()
     binding.load()
@@ -617,13 +618,18 @@ def guess_study(args):
             D0 = nets.guess(h)
             t_guess = time.perf_counter() - t0
             lrn = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess=D0)
+            # the same diagonal network without the pair blocks
+            lrd = h.scf(precision=prec, slices=3, incremental=1, approx_diag=1, guess=h.mlp_guess(nets.diag, bf16=True))
         rows.append({"waters": w, "seed": seed, "iterations_core": core["iterations"],
                      "iterations_sad": sadr["iterations"], "iterations_learned": lrn["iterations"],
+                     "iterations_learned_diag": lrd["iterations"],
                      "t_scf_core_s": core["t_total_s"], "t_scf_sad_s": sadr["t_total_s"],
                      "t_scf_learned_s": lrn["t_total_s"] + t_guess,
                      "dE_learned_vs_core": lrn["energy"] - core["energy"],
+                     "dE_learned_diag_vs_core": lrd["energy"] - core["energy"],
                      "dE_sad_vs_core": sadr["energy"] - core["energy"],
-                     "converged": bool(core["converged"] and lrn["converged"] and sadr["converged"])})
+                     "converged": bool(core["converged"] and lrn["converged"] and sadr["converged"]
+                                       and lrd["converged"])})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)   # progress, one line per held-out cluster
     nets.close()
     it_c = [r["iterations_core"] for r in rows]
@@ -633,11 +639,13 @@ def guess_study(args):
                       "eval_clusters": n_eval, "eval_range": [lo, hi], "mean_iterations_core": float(np.mean(it_c)),
                       "mean_iterations_sad": float(np.mean(it_s)),
                       "mean_iterations_learned": float(np.mean(it_l)),
+                      "mean_iterations_learned_diag_only": float(np.mean([r["iterations_learned_diag"] for r in rows])),
                       "iterations_saved_vs_core": 1.0 - float(np.sum(it_l)) / float(np.sum(it_c)),
                       "iterations_saved_vs_sad": 1.0 - float(np.sum(it_l)) / float(np.sum(it_s)),
                       "time_saved_vs_sad": 1.0 - float(sum(r["t_scf_learned_s"] for r in rows))
                                            / float(sum(r["t_scf_sad_s"] for r in rows)),
-                      "max_abs_dE_learned_vs_core": float(max(abs(r["dE_learned_vs_core"]) for r in rows)),
+                      "max_abs_dE_learned_vs_core": float(max(max(abs(r["dE_learned_vs_core"]),
+                                                                   abs(r["dE_learned_diag_vs_core"])) for r in rows)),
                       "max_abs_dE_sad_vs_core": float(max(abs(r["dE_sad_vs_core"]) for r in rows)),
                       "all_converged": all(r["converged"] for r in rows), "clusters": rows}))
 
