@@ -292,9 +292,12 @@ def gpu_arm(args):
         for label, p, g, inc_ in runs:
             res = h.scf(precision=p, slices=3, incremental=inc_, approx_diag=inc_,
                         guess=g if g is None or isinstance(g, str) else g[0])
-            hist[label] = h.history()[:, 1]
+            hrows = h.history()
+            hist[label] = hrows[:, 1]
             ttc[label] = t_build + res["t_total_s"] + (g[1] if isinstance(g, tuple) else 0.0)
             scf_info[label] = _scf_info(res)
+            # the last iterations' energy change and largest DIIS error element
+            scf_info[label]["last_dE_err"] = [[float(f"{r[2]:.3g}"), float(f"{r[3]:.3g}")] for r in hrows[-6:]]
 
     peaks, peak_src = _peaks()
     keys = ["gamma_ms", "coulomb_ms", "ytransform_ms", "kcontract_ms", "split_ms", "split_y_ms", "split_k_ms",
@@ -817,8 +820,8 @@ def main():
                     help="skip the plain FP64 SCF to convergence (FP64 whitening and exchange; minutes)")
     ap.add_argument("--no-c2", dest="c2", action="store_false", help="skip the 40-water measurement")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false")
-    ap.add_argument("--batch", type=int, default=16, help="molecules in the batched-SCF measurement (0: skip)")
-    ap.add_argument("--batch-max-waters", type=int, default=8, help="cluster sizes 1..W in the batched measurement")
+    ap.add_argument("--batch", type=int, default=256, help="molecules in the batched-SCF measurement (0: skip)")
+    ap.add_argument("--batch-max-waters", type=int, default=16, help="cluster sizes 1..W in the batched measurement")
     ap.add_argument("--guess-study", default=None, metavar="NTRAIN,NEVAL",
                     help="only the learned-guess study on held-out clusters (one JSON line)")
     ap.add_argument("--guess-epochs", type=int, default=200)

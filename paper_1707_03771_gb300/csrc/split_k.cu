@@ -595,10 +595,11 @@ bool use_tensor_cores() {
     return !(v && v[0] == '0');
 }
 
-// the tensor-core Y reads B's slices as packed lower 128-tiles (DFHF_TC_PACKED=1) or as full rows
+// the tensor-core Y reads B's slices as packed lower 128-tiles, or as full rows with DFHF_TC_PACKED=0 (half
+// the memory: 40 waters keep every slice resident; tests compare the two)
 bool use_packed_slices() {
     const char* v = std::getenv("DFHF_TC_PACKED");
-    return v && v[0] == '1';
+    return !(v && v[0] == '0');
 }
 
 }  // namespace

@@ -129,3 +129,35 @@ def test_blocked_slices_match_resident_slices(lib, rows):
     assert np.array_equal(again5, resident)
     scale = np.abs(K64).max()
     assert np.abs(blocked3 - K64).max() <= 2.0 ** (7 - 21) * scale
+
+
+@pytest.mark.parametrize("name", ["water2", "water8"])
+def test_packed_and_full_slice_layouts(lib, name):
+    """B's slices as packed lower 128-tiles (one exponent per auxiliary row; tiles above the diagonal read as
+    MN-major operands; at 8 waters np = 448 leaves a zero-padded half tile) against full rows (one exponent
+    per (P, mu)): both within the splitting bound 2^(7 - 7S) of FP64, within twice it of each other, and
+    the packed path bitwise reproducible."""
+    system = clusters.workload(name)
+    rng = np.random.default_rng(21)
+    out = {}
+    with lib.Handle(system) as h:
+        h.build_B()
+        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+        D = 2 * C @ C.T
+        K64 = h.jk(D, C, lib.DF_PREC_FP64)[1]
+        for packed in ("1", "0", "1"):
+            os.environ["DFHF_TC_PACKED"] = packed
+            try:
+                out.setdefault(packed, []).append({S: _k(h, lib, D, C, S, tc=True) for S in (3, 5)})
+            finally:
+                del os.environ["DFHF_TC_PACKED"]
+    scale = np.abs(K64).max()
+    for S in (3, 5):
+        bound = 2.0 ** (7 - 7 * S)
+        kp, kf = out["1"][0][S], out["0"][0][S]
+        print(f"{name} S={S}: packed {np.abs(kp - K64).max() / scale:.2e}, full rows {np.abs(kf - K64).max() / scale:.2e}")
+        assert np.abs(kp - K64).max() <= bound * scale
+        assert np.abs(kf - K64).max() <= bound * scale
+        assert np.abs(kp - kf).max() <= 2 * bound * scale
+        assert np.array_equal(kp, out["1"][1][S])
+        assert np.abs(kp - kp.T).max() == 0.0
