@@ -489,8 +489,10 @@ def estimate_bytes(system, precision=DF_PREC_FP64, slices=5) -> int:
     row = nt * (nt + 1) // 2 * 64 * 64
     total = 2 * naux * row * 8 + 40 * n * n * 8
     if precision == DF_PREC_SPLIT:
+        # B slices as packed lower 128-tiles (the tensor-core layout), Y and its slices
         ldy = (nocc + 31) // 32 * 32
-        total += slices * naux * npad * npad * 2 + naux * npad * ldy * (8 + 2 * slices)
+        nb = (n + 127) // 128
+        total += slices * naux * (nb * (nb + 1) // 2) * 128 * 128 * 2 + naux * npad * ldy * (8 + 2 * slices)
     return int(total)
 
 
