@@ -11,6 +11,7 @@
 // host each iteration for the convergence test. The symmetric eigensolver is cuSOLVER's dsyevd.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -1411,27 +1412,54 @@ int scf_drive_batch(df_handle** hs, int nmol, const df_options* o, df_result* rs
                 sad_factor(hs[i], factors[i], m0);
                 runs[i]->set_initial_factor(factors[i].p, m0);
             }
+        // DFHF_BATCH_TRACE=1: host time per part of the loop, printed to stderr at the end
+        const char* tv = std::getenv("DFHF_BATCH_TRACE");
+        const bool trace = tv && tv[0] == '1';
+        double t_begin = 0, t_finish = 0, t_enqueue = 0, t_idle = 0;
+        long long n_iter = 0;
+        using tclk = std::chrono::steady_clock;
+        auto since = [](tclk::time_point a) { return std::chrono::duration<double>(tclk::now() - a).count(); };
+        const auto t_all = tclk::now();
         int started = 0, finished = 0;
         while (finished < nmol) {
             bool progressed = false;
             for (int i = 0; i < started; ++i) {
                 ScfRun& r = *runs[i];
                 if (r.done() || !r.ready()) continue;
+                auto t0 = tclk::now();
                 r.finish_iteration();
-                if (r.done())
+                t_finish += since(t0);
+                ++n_iter;
+                if (r.done()) {
                     ++finished;
-                else
+                } else {
+                    t0 = tclk::now();
                     r.enqueue_iteration();
+                    t_enqueue += since(t0);
+                }
                 progressed = true;
             }
             if (started < nmol) {
+                auto t0 = tclk::now();
                 runs[started]->begin();
+                t_begin += since(t0);
+                t0 = tclk::now();
                 runs[started]->enqueue_iteration();
+                t_enqueue += since(t0);
                 ++started;
                 progressed = true;
             }
-            if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+            if (!progressed) {
+                const auto t0 = tclk::now();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                t_idle += since(t0);
+            }
         }
+        if (trace)
+            std::fprintf(stderr,
+                         "batch trace: %d molecules, %lld iterations, %.3f s: begin (B build, orthogonaliser) %.3f s, "
+                         "finish %.3f s, enqueue %.3f s, waiting %.3f s\n",
+                         nmol, n_iter, since(t_all), t_begin, t_finish, t_enqueue, t_idle);
         for (auto& r : runs)
             if (r->status() != DF_OK && status == DF_OK) status = r->status();
     } catch (...) {
