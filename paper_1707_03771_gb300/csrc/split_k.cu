@@ -595,11 +595,15 @@ bool use_tensor_cores() {
     return !(v && v[0] == '0');
 }
 
-// the tensor-core Y reads B's slices as packed lower 128-tiles, or as full rows with DFHF_TC_PACKED=0 (half
-// the memory: 40 waters keep every slice resident; tests compare the two)
-bool use_packed_slices() {
+// B slice layout for the tensor-core Y: full rows (one exponent per (P, mu): the smaller splitting error)
+// when every row's slices fit in HBM, else packed lower 128-tiles (half the memory: 40 waters keep every
+// slice resident); DFHF_TC_PACKED=1 / 0 forces packed / full rows (tests compare the two). Returns 1, 0, or
+// -1 for the automatic choice.
+int packed_preference() {
     const char* v = std::getenv("DFHF_TC_PACKED");
-    return !(v && v[0] == '0');
+    if (v && v[0] == '1') return 1;
+    if (v && v[0] == '0') return 0;
+    return -1;
 }
 
 }  // namespace
@@ -970,8 +974,9 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
     SplitState* st = h->split;
     // the tensor-core kernels read the packed slice layout, the mma.sync kernels the full one: a build of the
     // other kind re-cuts the slices (tests switch kernels on one handle; an SCF stays with one kind)
-    const bool want_packed = use_tensor_cores() && use_packed_slices() && (slices == 3 || slices == 5);
-    if (st && (st->S < slices || st->packed != want_packed)) {
+    const bool tc_ok = use_tensor_cores() && (slices == 3 || slices == 5);
+    const int pref = packed_preference();
+    if (st && (st->S < slices || (st->packed && !tc_ok) || (pref >= 0 && st->packed != (tc_ok && pref == 1)))) {
         free_split(h);
         st = nullptr;
     }
@@ -985,7 +990,6 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         st = new SplitState();
         h->split = st;
         st->np = h->pk.np;
-        st->packed = want_packed;
         st->nB = (st->np + 127) / 128;
         st->ntile = (long long)st->nB * (st->nB + 1) / 2;
         const long long np = st->np;
@@ -998,10 +1002,13 @@ void exchange_split(df_handle* h, const double* dC, int nocc, int slices, double
         DF_CUDA(cudaMemGetInfo(&free_b, &total_b));
         // SMAX slices of every auxiliary row when they fit beside Y and its slices; otherwise SMAX slices
         // of blocks of rows, cut from B at each build
-        const double row_slices = 2.0 * SMAX * row_elems(st);                // one row, every slice
         const double ybytes = (8.0 + 2.0 * SMAX) * h->naux * np * ldy;      // Y and its slices
         // kept free: working space (FP64 builds on the same handle use the split Y buffer)
         const double slack = 16.0 * np * np + (4ull << 30);
+        if (!tc_ok) st->packed = false;
+        else if (pref >= 0) st->packed = pref == 1;
+        else st->packed = (double)free_b <= 2.0 * SMAX * np * np * h->naux + ybytes + slack;
+        const double row_slices = 2.0 * SMAX * row_elems(st);                // one row, every slice
         st->S = SMAX;
         // DFHF_SPLIT_BLOCK_ROWS=r forces blocks of r rows (tests compare the two modes)
         const char* fb = std::getenv("DFHF_SPLIT_BLOCK_ROWS");

@@ -1,7 +1,7 @@
 """The tcgen05 (TMEM + TMA) split-precision kernels against the mma.sync split kernels and the FP64
-path on the same B and C. The tensor-core path cuts B into its lower 128 x 128 tiles with one exponent
-per auxiliary row (the tiles above the diagonal are read transposed), the mma.sync path into full rows
-with one exponent per (P, mu); both cut C the same way. They re-slice Y with exponents over different
+path on the same B and C. B's slices are full rows with one exponent per (P, mu) where they fit in HBM
+(every size here) and packed lower 128 x 128 tiles with one exponent per auxiliary row otherwise (the
+tiles above the diagonal read transposed; forced with DFHF_TC_PACKED=1); C is cut the same way. They re-slice Y with exponents over different
 blocks of the (P, i) contraction (the tensor-core contraction over chunks of the contiguous index
 P ldy + i, the mma.sync one over whole auxiliary rows), so their K differ by the splitting error: each is
 held to the bound 2^(7 - 7S) against FP64, and the two to twice it."""
@@ -103,28 +103,34 @@ def test_tile_widths_give_identical_exchange(lib, slices):
         assert np.array_equal(v, ref), k
 
 
+@pytest.mark.parametrize("packed", ["0", "1"])
 @pytest.mark.parametrize("rows", ["100", "1"])
-def test_blocked_slices_match_resident_slices(lib, rows):
+def test_blocked_slices_match_resident_slices(lib, rows, packed):
     """When B's slices do not fit in HBM they are cut per block of auxiliary rows at every build; at 5
     slices the digits are the same as with every row resident, so K is bitwise identical. Blocks of 100
-    rows (ragged last block: 1096 = 10 * 100 + 96) and of 1 row; the second build reuses the buffer."""
+    rows (ragged last block: 1096 = 10 * 100 + 96) and of 1 row; the second build reuses the buffer; full
+    rows and packed tiles (whose zero padding must survive the ragged last block)."""
     system = clusters.workload("water8")
     rng = np.random.default_rng(8)
-    with lib.Handle(system) as h:
-        h.build_B()
-        C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
-        D = 2 * C @ C.T
-        K64 = h.jk(D, C, lib.DF_PREC_FP64)[1]
-        resident = _k(h, lib, D, C, 5, tc=True)
-    with lib.Handle(system) as h:
-        h.build_B()
-        os.environ["DFHF_SPLIT_BLOCK_ROWS"] = rows
-        try:
-            blocked5 = _k(h, lib, D, C, 5, tc=True)
-            blocked3 = _k(h, lib, D, C, 3, tc=True)
-            again5 = _k(h, lib, D, C, 5, tc=True)
-        finally:
-            del os.environ["DFHF_SPLIT_BLOCK_ROWS"]
+    os.environ["DFHF_TC_PACKED"] = packed
+    try:
+        with lib.Handle(system) as h:
+            h.build_B()
+            C = np.linalg.qr(rng.normal(size=(h.n, h.nocc)))[0]
+            D = 2 * C @ C.T
+            K64 = h.jk(D, C, lib.DF_PREC_FP64)[1]
+            resident = _k(h, lib, D, C, 5, tc=True)
+        with lib.Handle(system) as h:
+            h.build_B()
+            os.environ["DFHF_SPLIT_BLOCK_ROWS"] = rows
+            try:
+                blocked5 = _k(h, lib, D, C, 5, tc=True)
+                blocked3 = _k(h, lib, D, C, 3, tc=True)
+                again5 = _k(h, lib, D, C, 5, tc=True)
+            finally:
+                del os.environ["DFHF_SPLIT_BLOCK_ROWS"]
+    finally:
+        del os.environ["DFHF_TC_PACKED"]
     assert np.array_equal(blocked5, resident)
     assert np.array_equal(again5, resident)
     scale = np.abs(K64).max()
