@@ -298,6 +298,16 @@ __global__ void transpose_kernel(const double* __restrict__ A, int n, double* __
     T[idx] = A[(long long)j * n + i];
 }
 
+// FP64 <-> FP32 copies (the mixed-precision eigensolve)
+__global__ void to_float_kernel(const double* __restrict__ a, long long len, float* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) b[i] = (float)a[i];
+}
+__global__ void to_double_kernel(const float* __restrict__ a, long long len, double* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) b[i] = (double)a[i];
+}
+
 // a += b
 __global__ void add_inplace_kernel(double* __restrict__ a, const double* __restrict__ b, long long len) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -500,6 +510,8 @@ class ScfRun {
         if (o_.approx_diag) {
             const long long no = nocc_, nv = nX_ - nocc_;
             DF_CUDA(cudaMalloc((void**)&abuf_, sizeof(double) * (3 * no * nX_ + no * nv + 2 * no * no)));
+            DF_CUDA(cudaMalloc((void**)&f32a_, sizeof(float) * ((long long)nX_ * nX_ + nX_)));
+            f32w_ = f32a_ + (long long)nX_ * nX_;
         }
         present_.assign(DIIS_MAX, 0);
         order_.clear();
@@ -714,7 +726,7 @@ class ScfRun {
             if (late_) diag_since_full_ = 0;
         }
         first_factor_ = false;
-        last_approx_ = approx;
+        last_approx_ = approx || mixed_step_;
     }
 
     int status() const { return status_; }
@@ -819,8 +831,40 @@ class ScfRun {
     }
 
     // Roothaan step on the orthogonal-basis Fock matrix held in Fp_: eigenvectors in place (row j of the
-    // row-major view is eigenvector j, ascending), the nocc lowest occupied
+    // row-major view is eigenvector j, ascending), the nocc lowest occupied. With options.approx_diag (and
+    // integer occupations) the eigensolve is FP32 (cuSOLVER's FP64 eigensolver takes 3-4x longer at
+    // n = 1600-2000 and holds the host thread while it runs) and is refined against the FP64 matrix by one
+    // rotation of the occupied-virtual block and the re-orthonormalisation of approx_orth: the FP32
+    // eigenvectors' errors (about 1e-6) enter the occupied space at second order. The orbital energies
+    // keep FP32 accuracy (they only scale the rotation); the final orbitals and energies are refreshed in
+    // FP64 when the run ends.
     void solve_orth() {
+        if (o_.approx_diag && !frac_ && nX_ > nocc_) {
+            const long long no = (long long)nX_ * nX_;
+            DF_CUDA(cudaMemcpyAsync(h_->work3.p, Fp_, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+            to_float_kernel<<<nblk(no), 256, 0, s_>>>(Fp_, no, f32a_);
+            DF_CHECK_LAUNCH();
+            int lw = 0;
+            DF_SOLVER(cusolverDnSsyevd_bufferSize(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, nX_, f32a_,
+                                                  nX_, f32w_, &lw));
+            if (lw > f32lwork_) {
+                if (f32work_) cudaFree(f32work_);
+                f32work_ = nullptr;
+                DF_CUDA(cudaMalloc((void**)&f32work_, sizeof(float) * lw));
+                f32lwork_ = lw;
+            }
+            DF_SOLVER(cusolverDnSsyevd(h_->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, nX_, f32a_, nX_,
+                                       f32w_, f32work_, f32lwork_, info_));
+            to_double_kernel<<<nblk(no), 256, 0, s_>>>(f32a_, no, Fp_);
+            DF_CHECK_LAUNCH();
+            to_double_kernel<<<nblk(nX_), 256, 0, s_>>>(f32w_, nX_, h_->eps.p);
+            DF_CHECK_LAUNCH();
+            fock_basis_ = true;
+            approx_orth(h_->work3.p);
+            mixed_step_ = true;
+            return;
+        }
+        mixed_step_ = false;
         eig(Fp_, nX_, h_->eps.p);
         vt_ = Fp_;
         fock_basis_ = true;
@@ -943,6 +987,10 @@ class ScfRun {
         if (Fo_) cudaFree(Fo_);
         if (abuf_) cudaFree(abuf_);
         abuf_ = nullptr;
+        if (f32a_) cudaFree(f32a_);
+        if (f32work_) cudaFree(f32work_);
+        f32a_ = f32w_ = f32work_ = nullptr;
+        f32lwork_ = 0;
         if (vto_) cudaFree(vto_);
         vto_ = wocc_ = nullptr;
         if (Kref_) cudaFree(Kref_);
@@ -981,6 +1029,9 @@ class ScfRun {
     double *Kref_ = nullptr, *Cref_ = nullptr, *Wq_ = nullptr, *core_ = nullptr;   // incremental Fock state
     bool late_ = false;            // past the max|e| < 1e-4 point (split: the 5-slice builds)
     double* abuf_ = nullptr;       // approximate diagonalisation scratch
+    float *f32a_ = nullptr, *f32w_ = nullptr, *f32work_ = nullptr;   // FP32 eigensolve: matrix, values, workspace
+    int f32lwork_ = 0;
+    bool mixed_step_ = false;      // the last full Roothaan step was the FP32 eigensolve with FP64 refinement
     bool fock_basis_ = false;      // Fp_ holds eigenvectors of a Fock matrix (eps their energies)
     bool last_approx_ = false;     // the last Roothaan step was approximate
     int diag_since_full_ = -1;     // late approximate steps since the last full eigensolve (-1: none yet)
