@@ -835,9 +835,9 @@ class ScfRun {
     // integer occupations) the eigensolve is FP32 (cuSOLVER's FP64 eigensolver takes 3-4x longer at
     // n = 1600-2000 and holds the host thread while it runs) and is refined against the FP64 matrix by one
     // rotation of the occupied-virtual block and the re-orthonormalisation of approx_orth: the FP32
-    // eigenvectors' errors (about 1e-6) enter the occupied space at second order. The orbital energies
-    // keep FP32 accuracy (they only scale the rotation); the final orbitals and energies are refreshed in
-    // FP64 when the run ends.
+    // eigenvectors' errors (about 1e-6) enter the occupied space at second order, and the virtual rows are
+    // projected out of the occupied space. The orbital energies keep FP32 accuracy (they only scale the
+    // rotations); the final orbitals and energies are refreshed in FP64 when the run ends.
     void solve_orth() {
         if (o_.approx_diag && !frac_ && nX_ > nocc_) {
             const long long no = (long long)nX_ * nX_;
@@ -861,6 +861,15 @@ class ScfRun {
             DF_CHECK_LAUNCH();
             fock_basis_ = true;
             approx_orth(h_->work3.p);
+            // the virtual rows made exactly orthogonal to the refined occupied rows: FP32 rows are orthogonal
+            // only to about 1e-7, and the late rotations, whose stationarity condition is F'_ia = 0 over these
+            // rows, would otherwise stop at a commutator floor of that order times |F|
+            const int nocc = nocc_, nv = nX_ - nocc_;
+            double* Vo = Fp_;
+            double* Vv = Fp_ + (long long)nocc * nX_;
+            double* O = h_->work1.p;   // nv x nocc
+            mm(s_, false, true, nv, nocc, nX_, 1.0, Vv, nX_, Vo, nX_, 0.0, O, nocc);
+            mm(s_, false, false, nv, nX_, nocc, -1.0, O, nocc, Vo, nX_, 1.0, Vv, nX_);
             mixed_step_ = true;
             return;
         }
