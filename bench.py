@@ -123,8 +123,9 @@ def _peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel and tile on the same workload;
-# keyed by (workload, kernel, slices, tile width). Anything not captured reports null.
-NCU_TRAFFIC = {}
+# keyed by (workload, kernel, slices, tile width). Anything not captured reports null. 32 waters, B slices as
+# full rows, Y and K 32 columns, K split 4 (one pass per launch).
+NCU_TRAFFIC = {("water32", "Y", 5, 32): 114.57e9 + 8.97e9, ("water32", "K", 5, 32): 27.58e9 + 0.04341e9}
 
 def core_density(h):
     """A physical density for the timed builds: the core-Hamiltonian orbitals of the handle's molecule."""
