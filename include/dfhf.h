@@ -87,8 +87,12 @@ typedef struct {
     int approx_diag;         /* 1: late iterations (max|e| < 1e-4) rotate the previous orbitals by
                                 kappa_ia = F'_ia / (eps_a - eps_i) (approximate diagonalisation, Stewart,
                                 Csaszar and Pulay 1982) instead of a full eigensolve; every 8th late
-                                iteration diagonalises in full. The result is unchanged (convergence is
-                                tested on the exact commutator). 0: full eigensolve every iteration. */
+                                iteration diagonalises in full. The full eigensolves then run in FP32 and
+                                are refined against the FP64 Fock matrix by one such rotation (and the
+                                virtual orbitals projected out of the occupied space); the reported
+                                orbitals and energies come from one FP64 eigensolve at the end. The result
+                                is unchanged (convergence is tested on the exact commutator). 0: full FP64
+                                eigensolve every iteration. */
 } df_options;
 
 typedef struct {
