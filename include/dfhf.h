@@ -1,5 +1,6 @@
 /*
- * dfhf.h -- C ABI of the GB300 density-fitted restricted Hartree-Fock library (libdfhf.so).
+ * dfhf.h -- C ABI of the GB300 density-fitted Hartree-Fock library (libdfhf.so): restricted Hartree-Fock,
+ * with unrestricted and restricted open-shell runs on the same builders.
  *
  * What the library computes (paper, arXiv:1707.03771):
  *   - every mean-field algorithm rests on density fitting (section "Program features");
@@ -27,7 +28,7 @@
  *   - Host threads: calls on one handle must not overlap (one thread at a time per handle; the handle's
  *     buffers, stream and solver state are not locked). Calls on different handles may run concurrently
  *     from several threads: the process-wide state (the Rys root table, the autotuner's tile choices, the
- *     tensor-map encoder entry point) is guarded by mutexes, and each handle owns its stream, its cuSOLVER
+ *     tensor-map encoder entry point, the atomic factors of the SAD guess) is guarded by mutexes, and each handle owns its stream, its cuSOLVER
  *     handle and its device buffers. The one shared device buffer is df_coulomb_noalloc's scratch (see
  *     there). scf_run_batch drives many handles from the calling thread alone.
  */
