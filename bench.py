@@ -665,6 +665,44 @@ def _oracle_scf_child(name):
     print(json.dumps({"t_s": time.perf_counter() - t0, "energy": r.energy, "iterations": r.iterations}))
 
 
+def open_shell_study(args):
+    """DF-UHF and DF-ROHF on the GPU: for each named workload, the cation (one electron removed: a doublet)
+    with B built once, UHF and ROHF to convergence in FP64 and in split precision (3 slices, then 5). Prints
+    one JSON line with times, iterations, energies and <S^2>."""
+    import copy
+
+    from paper_1707_03771_gb300 import binding, build, clusters
+    build.build()
+    binding.load()
+    rows = []
+    for name in args.open_shell.split(","):
+        system = copy.deepcopy(clusters.workload(name))
+        system.charge = 1
+        ne = system.n_electrons
+        na, nb = (ne + 1) // 2, ne // 2
+        with binding.Handle(system, open_shell=True) as h:
+            t0 = time.perf_counter()
+            h.build_B()
+            t_build = time.perf_counter() - t0
+            row = {"workload": name, "n": h.n, "naux": h.naux, "nalpha": na, "nbeta": nb, "t_build_B_s": t_build}
+            # FP64 exchange builds up to 800 basis functions (at 1600 one FP64 iteration of UHF takes ~10 s)
+            precs = (("fp64", binding.DF_PREC_FP64), ("split", binding.DF_PREC_SPLIT)) if h.n <= 800 else \
+                (("split", binding.DF_PREC_SPLIT),)
+            for label, prec in precs:
+                for kind in ("uhf", "rohf"):
+                    run = h.scf_uhf if kind == "uhf" else h.scf_rohf
+                    r = run(na, nb, precision=prec, slices=3)
+                    row[f"{kind}_{label}"] = {"energy": r["energy"], "iterations": r["iterations"],
+                                              "converged": bool(r["converged"]), "s2": r["s2"],
+                                              "t_total_s": r["t_total_s"], "t_jk_s": r["t_jk_s"]}
+            for kind in ("uhf", "rohf"):
+                if f"{kind}_fp64" in row:
+                    row[f"dE_{kind}_split_vs_fp64"] = row[f"{kind}_split"]["energy"] - row[f"{kind}_fp64"]["energy"]
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "DF-UHF and DF-ROHF of water-cluster cations", "workloads": rows}))
+
+
 def oracle_scf_study(args):
     """Whole SCF runs beside the oracle on the same host: for each workload, the GPU FP64 and split-precision
     SCF (B built and timed) and the oracle's DF-RHF on all host cores, and on one core for workloads of at
@@ -836,11 +874,15 @@ def main():
     ap.add_argument("--oracle-scf", default=None, metavar="WORKLOADS",
                     help="only whole SCF runs, GPU beside the oracle, e.g. water2,water8 (one JSON line)")
     ap.add_argument("--oracle-scf-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--open-shell", default=None, metavar="WORKLOADS",
+                    help="only DF-UHF and DF-ROHF of the cations of these workloads, e.g. water8,water32 (one JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.oracle_scf_child:
         _oracle_scf_child(args.oracle_scf_child)
+    elif args.open_shell:
+        open_shell_study(args)
     elif args.oracle_scf:
         oracle_scf_study(args)
     elif args.guess_study:
