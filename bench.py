@@ -689,13 +689,16 @@ def open_shell_study(args):
             precs = (("fp64", binding.DF_PREC_FP64), ("split", binding.DF_PREC_SPLIT)) if h.n <= 800 else \
                 (("split", binding.DF_PREC_SPLIT),)
             for label, prec in precs:
-                for kind in ("uhf", "rohf"):
-                    run = h.scf_uhf if kind == "uhf" else h.scf_rohf
-                    r = run(na, nb, precision=prec, slices=3)
+                # UHF from the core Hamiltonian, ROHF, then UHF from the ROHF spin densities
+                for kind in ("uhf", "rohf", "uhf_from_rohf"):
+                    if kind == "rohf":
+                        r = h.scf_rohf(na, nb, precision=prec, slices=3)
+                    else:
+                        r = h.scf_uhf(na, nb, precision=prec, slices=3, guess="spin" if kind != "uhf" else "core")
                     row[f"{kind}_{label}"] = {"energy": r["energy"], "iterations": r["iterations"],
                                               "converged": bool(r["converged"]), "s2": r["s2"],
                                               "t_total_s": r["t_total_s"], "t_jk_s": r["t_jk_s"]}
-            for kind in ("uhf", "rohf"):
+            for kind in ("uhf", "rohf", "uhf_from_rohf"):
                 if f"{kind}_fp64" in row:
                     row[f"dE_{kind}_split_vs_fp64"] = row[f"{kind}_split"]["energy"] - row[f"{kind}_fp64"]["energy"]
         rows.append(row)

@@ -66,14 +66,16 @@ typedef struct { int atom; int l; double exponent; double center[3]; } df_shell;
 #define DF_GUESS_CORE 0      /* core-Hamiltonian guess */
 #define DF_GUESS_SAD 1       /* superposition of atomic densities (df_sad_density): the first Fock matrix is
                                 built from that density itself */
+#define DF_GUESS_SPIN 2      /* scf_run_uhf only: the natural orbitals of the spin densities of the handle's last
+                                scf_run_uhf / scf_run_rohf (e.g. UHF from the ROHF solution) */
 
 typedef struct {
     double conv_E;           /* |E_n - E_{n-1}| threshold (hartree), e.g. 1e-10 */
     double conv_err;         /* max |X^T (F D S - S D F) X| threshold, e.g. 1e-7 */
     int max_iter;            /* iteration cap */
     int diis_size;           /* Pulay subspace (<= 16) */
-    int guess;               /* DF_GUESS_CORE or DF_GUESS_SAD (else DF_E_ARG); scf_run_guess's D0 takes
-                                precedence */
+    int guess;               /* DF_GUESS_CORE or DF_GUESS_SAD (DF_GUESS_SPIN for scf_run_uhf; else DF_E_ARG);
+                                scf_run_guess's D0 takes precedence */
     int precision;           /* DF_PREC_* */
     int slices;              /* BF16 slices per operand for DF_PREC_SPLIT (2..5) in early iterations;
                                 once max|e| < 1e-4 the exchange is built with 5 slices, and the SCF
@@ -209,7 +211,8 @@ int df_sad_density(df_handle* h, double* D0);
  * E = 1/2 tr(D_a(H + F_a)) + 1/2 tr(D_b(H + F_b)) + E_nuc, Pulay DIIS over the pair of orthogonal-basis Fock
  * matrices with errors X^T(F_s D_s S - S D_s F_s)X, core-Hamiltonian start for both spins, convergence as
  * scf_run on the larger of the two errors. out->s2 = <S^2>. Requires nalpha >= nbeta >= 0 and
- * nalpha + nbeta = electron count (DF_E_ARG otherwise); options.guess must be DF_GUESS_CORE, incremental and
+ * nalpha + nbeta = electron count (DF_E_ARG otherwise); options.guess DF_GUESS_CORE, or DF_GUESS_SPIN to start
+ * from the last open-shell run's spin densities (DF_E_STATE if the handle has none); incremental and
  * approx_diag 0. After the run df_get_matrix gives the total density (6) and the spin densities (12, 13). */
 int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_result* out);
 

@@ -15,7 +15,7 @@ from . import build as _build
 DF_OK, DF_E_ARG, DF_E_NOMEM, DF_E_CUDA, DF_E_NOTCONV, DF_E_STATE, DF_E_NUMERIC, DF_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 DF_PREC_FP64, DF_PREC_SPLIT = 0, 1
 DF_WHITEN_SPLIT, DF_WHITEN_FP64 = 0, 1
-DF_GUESS_CORE, DF_GUESS_SAD = 0, 1
+DF_GUESS_CORE, DF_GUESS_SAD, DF_GUESS_SPIN = 0, 1, 2
 
 EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_run", "df_get_rows", "df_get_matrix", "df_rys",
             "df_prepare", "df_set_stream", "df_timings", "df_free", "df_strerror", "df_last_error",
@@ -273,9 +273,13 @@ class Handle:
         return D0
 
     def scf_uhf(self, nalpha, nbeta, conv_E=1e-10, conv_err=1e-7, max_iter=200, diis_size=8, precision=DF_PREC_FP64,
-                slices=3, screen_tau=0.0):
-        """Unrestricted Hartree-Fock (scf_run_uhf) with nalpha and nbeta electrons."""
-        o = Options(conv_E, conv_err, max_iter, diis_size, DF_GUESS_CORE, precision, slices, 0, screen_tau, 0)
+                slices=3, screen_tau=0.0, guess="core"):
+        """Unrestricted Hartree-Fock (scf_run_uhf) with nalpha and nbeta electrons, from the core Hamiltonian
+        (guess="core") or from the spin densities of the last open-shell run on this handle (guess="spin")."""
+        if guess not in ("core", "spin"):
+            raise ValueError("guess: 'core' or 'spin'")
+        g = DF_GUESS_CORE if guess == "core" else DF_GUESS_SPIN
+        o = Options(conv_E, conv_err, max_iter, diis_size, g, precision, slices, 0, screen_tau, 0)
         r = Result()
         rc = load().scf_run_uhf(self.h, ctypes.byref(o), int(nalpha), int(nbeta), ctypes.byref(r))
         if rc not in (DF_OK, DF_E_NOTCONV):

@@ -654,10 +654,13 @@ int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_
     if (opts->max_iter < 1 || opts->conv_E <= 0 || opts->conv_err <= 0 || opts->screen_tau < 0) return DF_E_ARG;
     if (opts->precision != DF_PREC_FP64 && opts->precision != DF_PREC_SPLIT) return DF_E_ARG;
     if (opts->precision == DF_PREC_SPLIT && (opts->slices < 2 || opts->slices > 5)) return DF_E_ARG;
-    if (opts->guess != DF_GUESS_CORE || opts->incremental || opts->approx_diag)
-        return fail(h, Error{DF_E_ARG, "scf_run_uhf: core-Hamiltonian guess, full builds and full eigensolves only"});
+    if ((opts->guess != DF_GUESS_CORE && opts->guess != DF_GUESS_SPIN) || opts->incremental || opts->approx_diag)
+        return fail(h, Error{DF_E_ARG, "scf_run_uhf: core-Hamiltonian or spin-density guess, full builds and full "
+                                       "eigensolves only"});
     if (nalpha < nbeta || nbeta < 0 || nalpha + nbeta != h->nelec || nalpha > h->n)
         return fail(h, Error{DF_E_ARG, "scf_run_uhf: need nalpha >= nbeta >= 0, nalpha + nbeta = electron count"});
+    if (opts->guess == DF_GUESS_SPIN && !h->Dspin.p)
+        return fail(h, Error{DF_E_STATE, "scf_run_uhf: no spin densities of an earlier open-shell run on this handle"});
     try {
         DF_CUDA(cudaSetDevice(h->device));
         return scf_drive_uhf(h, opts, nalpha, nbeta, out);

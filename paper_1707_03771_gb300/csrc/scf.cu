@@ -1073,7 +1073,10 @@ class ScfRun {
 // 5-slice builds); F_s = H + J - K_s; E = 1/2 tr(D_a (H + F_a)) + 1/2 tr(D_b (H + F_b)) + E_nuc. Pulay DIIS
 // over the stacked pair (F'_a, F'_b) with errors F'_s P_s - P_s F'_s (P_s = V_s,occ V_s,occ^T; the
 // orthogonal-basis form of X^T (F_s D_s S - S D_s F_s) X), one set of coefficients for both spins;
-// core-Hamiltonian start for both spins; every step on the device in FP64 except the exchange contraction.
+// core-Hamiltonian start for both spins, or (options.guess = DF_GUESS_SPIN) the natural orbitals of the
+// spin densities of the handle's last open-shell run; every step on the device in FP64 except the exchange
+// contraction.
+
 // Restricted open-shell effective Fock matrix in the basis of the current orbitals (closed p < nb, open
 // nb <= p < na, virtual p >= na): closed-open pairs take F_b, open-virtual pairs F_a, all others
 // (F_a + F_b) / 2. Fa_mo becomes the effective matrix plus the level shift (lambda on the virtual,
@@ -1091,6 +1094,14 @@ __global__ void rohf_effective_kernel(double* __restrict__ Fa_mo, double* __rest
     Fb_mo[idx] = cp != cq ? f : 0.0;
     if (p == q) f += cp == 2 ? shift : (cp == 1 ? 0.5 * shift : 0.0);
     Fa_mo[idx] = f;
+}
+
+// out[r] = V[(r + shift) mod m] for the m rows of m entries: row `shift` of V becomes the first row of out
+__global__ void rotate_rows_kernel(const double* __restrict__ V, int m, int shift, double* __restrict__ out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * m) return;
+    const int r = (int)(idx / m), c = (int)(idx % m);
+    out[idx] = V[(long long)((r + shift) % m) * m + c];
 }
 
 // Unrestricted (two orbital sets) or restricted open-shell (one set: the beta orbitals are the first nb
@@ -1159,10 +1170,35 @@ class UhfRun {
         int* slotp = ints_ + 2 * DIIS_MAX + 3;
         std::vector<int> present(DIIS_MAX, 0), order;
         std::vector<int> ctl(2 * DIIS_MAX + 4, 0);
-        // core-Hamiltonian start for both spins
-        to_orth(h_->H.p, Fo_);
-        DF_CUDA(cudaMemcpyAsync(Fo_ + no, Fo_, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
-        roothaan(Fo_);
+        if (o_.guess == DF_GUESS_SPIN) {
+            // natural orbitals of the last run's spin densities: for each spin the eigenvectors of
+            // X^T S D_s S X, the n_s of largest occupation first
+            if (!h_->Dspin.p) throw Error{DF_E_STATE, "scf_run_uhf: no spin densities of an earlier open-shell run"};
+            for (int sp = 0; sp < 2; ++sp) {
+                const int nocc = sp == 0 ? na_ : nb_;
+                dgemm(s_, false, false, n_, n_, n_, 1.0, h_->S.p, n_, h_->Dspin.p + sp * nn_, n_, 0.0, h_->work1.p, n_);
+                dgemm(s_, false, false, n_, n_, n_, 1.0, h_->work1.p, n_, h_->S.p, n_, 0.0, h_->work2.p, n_);
+                to_orth(h_->work2.p, Fo_ + sp * no);
+                eig(Fo_ + sp * no, nX_, h_->eps.p + sp * n_);   // ascending: the occupied are the last rows
+                rotate_rows_kernel<<<nblk(no), 256, 0, s_>>>(Fo_ + sp * no, nX_, nX_ - nocc, V_ + sp * no);
+                DF_CHECK_LAUNCH();
+                double* C = C_ + (sp == 0 ? 0 : (long long)n_ * na_);
+                double* D = D_ + sp * nn_;
+                if (nocc > 0) {
+                    dgemm(s_, false, true, n_, nocc, nX_, 1.0, h_->X.p, nX_, V_ + sp * no, nX_, 0.0, C, nocc);
+                    dgemm(s_, false, true, n_, n_, nocc, 1.0, C, nocc, C, nocc, 0.0, D, n_);
+                } else {
+                    DF_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * nn_, s_));
+                }
+            }
+            add_kernel2<<<nblk(nn_), 256, 0, s_>>>(D_, D_ + nn_, nn_, D_ + 2 * nn_);
+            DF_CHECK_LAUNCH();
+        } else {
+            // core-Hamiltonian start for both spins
+            to_orth(h_->H.p, Fo_);
+            DF_CUDA(cudaMemcpyAsync(Fo_ + no, Fo_, sizeof(double) * no, cudaMemcpyDeviceToDevice, s_));
+            roothaan(Fo_);
+        }
         const auto t_iter = std::chrono::steady_clock::now();
         double e_old = 0.0, jk_ms = 0.0;
         int status = DF_E_NOTCONV;

@@ -107,3 +107,24 @@ def test_closed_shell_rohf_equals_rhf(lib, water2):
         r = h.scf()
         ro = h.scf_rohf(10, 10)
     assert ro["converged"] and abs(ro["energy"] - r["energy"]) <= 1e-9, (ro["energy"], r["energy"])
+
+
+def test_uhf_from_rohf_spin_densities(lib, water2):
+    """UHF started from the ROHF solution (DF_GUESS_SPIN): the ROHF determinant is one of UHF's, so the run
+    descends to an energy at or below ROHF's; a handle without an earlier open-shell run refuses the guess."""
+    import copy
+    system = copy.deepcopy(water2)
+    system.charge = 1
+    with lib.Handle(system, open_shell=True) as h:
+        h.build_B(whitening=lib.DF_WHITEN_FP64)
+        with pytest.raises(lib.DFError) as e:
+            h.scf_uhf(10, 9, guess="spin")
+        assert e.value.code == lib.DF_E_STATE
+        ro = h.scf_rohf(10, 9)
+        us = h.scf_uhf(10, 9, guess="spin")
+        uc = h.scf_uhf(10, 9)
+    print(f"ROHF {ro['energy']:.10f}, UHF from ROHF {us['energy']:.10f} ({us['iterations']} it), "
+          f"UHF from core-H {uc['energy']:.10f}")
+    assert ro["converged"] and us["converged"]
+    assert us["energy"] <= ro["energy"] + 1e-10
+    assert us["s2"] >= 0.75 - 1e-9
