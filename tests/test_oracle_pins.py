@@ -670,3 +670,82 @@ def test_rohf_converged_orbitals_are_stationary(water2_open, na, nb):
     for a, b, f in [(0, 1, -2.0), (1, 2, -2.0), (0, 2, -4.0)]:
         blk = np.ix_(cls == a, cls == b)
         assert np.abs(G[blk] - f * err[blk]).max() <= 1e-12 * max(1.0, np.abs(G[blk]).max())
+
+
+# closed-shell DF-MP2 (oracle/dfmp2.py)
+
+def test_mp2_h2_minimal_basis_closed_form():
+    """H2 with one s function per atom (the product-complete auxiliary set makes DF exact): one occupied
+    (sigma_g) and one virtual (sigma_u) orbital, fixed by symmetry, so E2 = (gu|gu)^2 / (2 (e_g - e_u)) with
+    e_g = h_gg + (gg|gg), e_u = h_uu + 2 (uu|gg) - (ug|ug), every integral from the s-type closed forms."""
+    from oracle import dfmp2
+    R, a = 1.4, 0.8
+    sysh = clusters.h2_system(R, alpha=a)
+    res = dfrhf.scf(sysh)
+    B = dfrhf.whiten(dfrhf.three_center(sysh), dfrhf.metric(sysh))
+    N = (2 * a / math.pi) ** 0.75
+    s12 = N * N * (math.pi / (2 * a)) ** 1.5 * math.exp(-a / 2 * R * R)
+    t11 = N * N * (a / 2) * 3 * (math.pi / (2 * a)) ** 1.5
+    t12 = N * N * (a / 2) * (3 - a * R * R) * (math.pi / (2 * a)) ** 1.5 * math.exp(-a / 2 * R * R)
+    F0 = lambda T: 1.0 if T == 0 else 0.5 * math.sqrt(math.pi / T) * erf(math.sqrt(T))
+    pref = 2 * math.pi / (2 * a)
+    v11 = -N * N * pref * (F0(0) + F0(2 * a * R * R))
+    v12 = -N * N * pref * math.exp(-a / 2 * R * R) * 2 * F0(2 * a * (R / 2) ** 2)
+    h = np.array([[t11 + v11, t12 + v12], [t12 + v12, t11 + v11]])
+    cen = np.array([0.0, R])
+
+    def ao(A, B_, C, D):
+        P = (cen[A] + cen[B_]) / 2
+        Q = (cen[C] + cen[D]) / 2
+        K = math.exp(-a / 2 * (cen[A] - cen[B_]) ** 2) * math.exp(-a / 2 * (cen[C] - cen[D]) ** 2)
+        p = q = 2 * a
+        return N ** 4 * 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * K * F0(p * q / (p + q) * (P - Q) ** 2)
+
+    eri = np.array([[[[ao(A, B_, C, D) for D in range(2)] for C in range(2)] for B_ in range(2)] for A in range(2)])
+    cg = np.array([1.0, 1.0]) / math.sqrt(2 * (1 + s12))
+    cu = np.array([1.0, -1.0]) / math.sqrt(2 * (1 - s12))
+
+    def mo(p, q, r, s):
+        return float(np.einsum("abcd,a,b,c,d->", eri, p, q, r, s))
+
+    e_g = cg @ h @ cg + mo(cg, cg, cg, cg)
+    e_u = cu @ h @ cu + 2 * mo(cu, cu, cg, cg) - mo(cu, cg, cu, cg)
+    e2_closed = mo(cg, cu, cg, cu) ** 2 / (2 * (e_g - e_u))
+    e2 = dfmp2.mp2_energy(B, res.C, res.eps, 1)
+    assert abs(res.eps[0] - e_g) < 1e-10 and abs(res.eps[1] - e_u) < 1e-10
+    assert e2 < 0 and abs(e2 - e2_closed) < 1e-12, (e2, e2_closed)
+
+
+@pytest.fixture(scope="module")
+def water2_mp2(water2_sys):
+    from oracle import dfmp2
+    B = dfrhf.whiten(dfrhf.three_center(water2_sys), dfrhf.metric(water2_sys))
+    res = dfrhf.scf(water2_sys, B=B)
+    return B, res, dfmp2.mp2_energy(B, res.C, res.eps, water2_sys.nocc)
+
+
+def test_mp2_closed_shell_form_equals_spin_orbital_form(water2_mp2, water2_sys):
+    """The closed-shell spin summation 2 (ia|jb) - (ib|ja) against the antisymmetrised spin-orbital sum
+    1/4 |<ij||ab>|^2 on the 2-water cluster: a swapped exchange index or a wrong factor fails it."""
+    from oracle import dfmp2
+    B, res, e2 = water2_mp2
+    e2_so = dfmp2.mp2_energy_spin_orbital(B, res.C, res.eps, water2_sys.nocc)
+    assert e2 < 0 and abs(e2 - e2_so) < 1e-11 * abs(e2), (e2, e2_so)
+
+
+def test_mp2_size_consistent():
+    """Two identical waters 3000 bohr apart: the correlation energy is twice the monomer's (MP2 is size
+    consistent; the dimer's orbitals pair up into degenerate sets, and E2 does not depend on how a
+    degenerate set is rotated). The remaining interaction falls off with distance (measured: 5e-8 Eh at
+    100 bohr, 2.8e-9 at 300, 1.1e-10 at 3000)."""
+    from oracle import dfmp2
+    mono = clusters.water_cluster(1, 5)
+    atoms = np.concatenate([mono.atoms, mono.atoms.copy()])
+    atoms["xyz"][3:] += np.array([0.0, 0.0, 3000.0])
+    dimer = clusters.make_system(atoms)
+    out = []
+    for s in (mono, dimer):
+        B = dfrhf.whiten(dfrhf.three_center(s), dfrhf.metric(s))
+        r = dfrhf.scf(s, B=B, conv_E=1e-13, conv_err=1e-11, max_iter=200)
+        out.append(dfmp2.mp2_energy(B, r.C, r.eps, s.nocc))
+    assert abs(out[1] - 2 * out[0]) < 1e-9, out
