@@ -706,6 +706,31 @@ def open_shell_study(args):
     print(json.dumps({"study": "DF-UHF and DF-ROHF of water-cluster cations", "workloads": rows}))
 
 
+def mp2_study(args):
+    """DF-MP2 on the GPU: for each named workload, B and the FP64 SCF, then df_mp2 of its canonical orbitals
+    (FP64). Prints one JSON line with times and energies."""
+    from paper_1707_03771_gb300 import binding, build, clusters
+    build.build()
+    binding.load()
+    rows = []
+    for name in args.mp2.split(","):
+        system = clusters.workload(name)
+        with binding.Handle(system) as h:
+            r = h.scf()
+            nmo = h.n - r["n_dropped"]
+            t0 = time.perf_counter()
+            e2 = h.mp2(n_dropped=r["n_dropped"])
+            t_mp2 = time.perf_counter() - t0
+            nocc, nvir = h.nocc, nmo - h.nocc
+            # FP64 work: the second transformation 2 naux nvir nocc n, the pair integrals over j <= i
+            flops = 2.0 * h.naux * nvir * nocc * h.n + 2.0 * nvir * nvir * h.naux * nocc * (nocc + 1) / 2
+            rows.append({"workload": name, "n": h.n, "naux": h.naux, "nocc": nocc, "nvir": nvir,
+                         "e_scf": r["energy"], "e_mp2_corr": e2, "t_scf_s": r["t_total_s"], "t_mp2_s": t_mp2,
+                         "mp2_fp64_gflop": flops / 1e9, "mp2_fp64_tflops": flops / t_mp2 / 1e12})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "DF-MP2 correlation energy (FP64) of water clusters", "workloads": rows}))
+
+
 def oracle_scf_study(args):
     """Whole SCF runs beside the oracle on the same host: for each workload, the GPU FP64 and split-precision
     SCF (B built and timed) and the oracle's DF-RHF on all host cores, and on one core for workloads of at
@@ -877,6 +902,8 @@ def main():
     ap.add_argument("--oracle-scf", default=None, metavar="WORKLOADS",
                     help="only whole SCF runs, GPU beside the oracle, e.g. water2,water8 (one JSON line)")
     ap.add_argument("--oracle-scf-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--mp2", default=None, metavar="WORKLOADS",
+                    help="only DF-MP2 after the FP64 SCF of these workloads, e.g. water8,water16 (one JSON line)")
     ap.add_argument("--open-shell", default=None, metavar="WORKLOADS",
                     help="only DF-UHF and DF-ROHF of the cations of these workloads, e.g. water8,water32 (one JSON line)")
     args = ap.parse_args()
@@ -886,6 +913,8 @@ def main():
         _oracle_scf_child(args.oracle_scf_child)
     elif args.open_shell:
         open_shell_study(args)
+    elif args.mp2:
+        mp2_study(args)
     elif args.oracle_scf:
         oracle_scf_study(args)
     elif args.guess_study:

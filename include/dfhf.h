@@ -228,6 +228,16 @@ int scf_run_uhf(df_handle* h, const df_options* opts, int nalpha, int nbeta, df_
 int scf_run_rohf(df_handle* h, const df_options* opts, int nalpha, int nbeta, double level_shift,
                  df_result* out);
 
+/* Density-fitted closed-shell MP2 correlation energy (paper, section "Program features": MP2 on the
+ * density-fitting utilities; eq. 1 applied to both orbital indices, eq. 2 second form):
+ *   B^P_ia = sum_{mu nu} C_mu i B_P,mu nu C_nu a, (ia|jb) = sum_P B^P_ia B^P_jb,
+ *   E2 = sum_{ij ab} (ia|jb) [2 (ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b), every orbital correlated,
+ * in FP64 on the GPU from the handle's B. C: host, n x nmo row-major, column k = canonical orbital k in
+ * ascending energy (the first nocc occupied; e.g. df_get_matrix 10 after scf_run, nmo = n - dropped); eps:
+ * host, nmo orbital energies. Requires B (DF_E_STATE), 1 <= nocc < nmo <= n (DF_E_ARG). Device memory:
+ * about 8 naux (np + 2 nmo) nocc bytes besides B. */
+int df_mp2(df_handle* h, const double* C, const double* eps, int nmo, int nocc, double* e2);
+
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
  * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric
  * (eigenvectors of X^T S D0 S X). Otherwise as scf_run. */

@@ -24,7 +24,7 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
             "df_fp64_rate", "df_sad_density", "df_build_B_batch",
             "df_init_open", "scf_run_uhf", "scf_run_rohf", "df_water_pairs", "df_pair_blocks", "df_pair_density",
-            "df_mlp_guess_pairs"]
+            "df_mlp_guess_pairs", "df_mp2"]
 DF_MLP_NFEAT = 57
 DF_MLP_NPFEAT = 26
 PAIR_CUTOFF = 7.5      # bohr, O-O distance of the water pairs whose blocks the pair network predicts
@@ -117,6 +117,7 @@ def load(path: str | None = None):
     L.df_pair_blocks.argtypes = [c_void_p, dp, ip, c_int, fp]
     L.df_pair_density.argtypes = [c_void_p, fp, ip, c_int, dp]
     L.df_mlp_guess_pairs.argtypes = [c_void_p, c_void_p, c_void_p, ctypes.c_double, c_int, dp]
+    L.df_mp2.argtypes = [c_void_p, dp, dp, c_int, c_int, dp]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -254,6 +255,21 @@ class Handle:
             self._check(load().df_mlp_guess_pairs(self.h, mlp.m, pair_mlp.m, float(cutoff), int(bf16), _dp(D0)),
                         "df_mlp_guess_pairs")
         return D0
+
+    def mp2(self, C=None, eps=None, nocc=None, n_dropped=0):
+        """DF-MP2 correlation energy (df_mp2) of the canonical orbitals C (n x nmo, columns ascending) with
+        energies eps; by default those of the last scf() on this handle (n_dropped: its result's
+        n_dropped)."""
+        if C is None:
+            nmo = self.n - n_dropped
+            C = self.matrix("C").reshape(-1)[: self.n * nmo].reshape(self.n, nmo)
+            eps = self.matrix("eps")[:nmo]
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        nocc = self.nocc if nocc is None else int(nocc)
+        e2 = ctypes.c_double()
+        self._check(load().df_mp2(self.h, _dp(C), _dp(eps), C.shape[1], nocc, ctypes.byref(e2)), "df_mp2")
+        return e2.value
 
     def pair_blocks(self, D, pairs):
         """Frame blocks (npairs x nb x nb, float32) of the ordered water pairs `pairs` (npairs x 2) of D."""

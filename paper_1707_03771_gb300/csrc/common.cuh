@@ -203,6 +203,9 @@ void jk_fp64(df_handle* h, const double* dD, const double* dC, int nocc, double*
 void ensure_jk_buffers(df_handle* h, int nocc);
 void coulomb_fp64(df_handle* h, const double* dD, double* dJ);
 void pad_occupied(df_handle* h, const double* dC, int nocc, int ldy);
+// Y_{P,mu i} = sum_nu B_{P,mu nu} C_{nu i} from the packed FP64 B (Y: naux x np x ldy)
+void y_transform_fp64(cudaStream_t s, const double* B, long long row, int nt, int naux, const double* Cp, int ldy,
+                      int ncol, double* Y);
 void exchange_fp64(df_handle* h, int nocc, double* dK);
 int k_splits(const df_handle* h);
 void unpack_rows(df_handle* h, const double* packed, int p0, int count, double* dout);
