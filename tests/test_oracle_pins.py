@@ -749,3 +749,89 @@ def test_mp2_size_consistent():
         r = dfrhf.scf(s, B=B, conv_E=1e-13, conv_err=1e-11, max_iter=200)
         out.append(dfmp2.mp2_energy(B, r.C, r.eps, s.nocc))
     assert abs(out[1] - 2 * out[0]) < 1e-9, out
+
+
+# density-fitting object operations, eqs. (1)-(3) (oracle/dfops.py)
+
+def test_dfops_brute_force_tiny():
+    """Every operation against nested loops over its defining sum, on tiny ragged tensors."""
+    from oracle import dfops
+    r = np.random.default_rng(31)
+    g, nr, ns, nt, nu = 3, 2, 3, 2, 4
+    I, I2, I3 = r.normal(size=(g, nr, ns)), r.normal(size=(g, nr, nt)), r.normal(size=(g, nt, nu))
+    Mr, Ms, Mp = r.normal(size=(nr, nt)), r.normal(size=(ns, nt)), r.normal(size=(5, g))
+    Mrs, D, G = r.normal(size=(nr, ns)), r.normal(size=g), r.normal(size=(nr * ns, nt * nu))
+    out = np.zeros((g, nt, ns))
+    for a in range(g):
+        for t in range(nt):
+            for s in range(ns):
+                out[a, t, s] = sum(I[a, k, s] * Mr[k, t] for k in range(nr))
+    assert np.allclose(dfops.transform_first(I, Mr), out, rtol=0, atol=1e-13)
+    out = np.zeros((g, nr, nt))
+    for a in range(g):
+        for k in range(nr):
+            for t in range(nt):
+                out[a, k, t] = sum(I[a, k, s] * Ms[s, t] for s in range(ns))
+    assert np.allclose(dfops.transform_second(I, Ms), out, rtol=0, atol=1e-13)
+    out = np.zeros((5, nr, ns))
+    for a in range(5):
+        out[a] = sum(Mp[a, d] * I[d] for d in range(g))
+    assert np.allclose(dfops.transform_aux(I, Mp), out, rtol=0, atol=1e-13)
+    out = np.zeros((ns, nt))
+    for s in range(ns):
+        for t in range(nt):
+            out[s, t] = sum(I[a, k, s] * I2[a, k, t] for a in range(g) for k in range(nr))
+    assert np.allclose(dfops.contract_first(I, I2), out, rtol=0, atol=1e-13)
+    out = np.zeros((nr * ns, nt * nu))
+    for k in range(nr):
+        for s in range(ns):
+            for t in range(nt):
+                for u in range(nu):
+                    out[k * ns + s, t * nu + u] = sum(I[a, k, s] * I3[a, t, u] for a in range(g))
+    assert np.allclose(dfops.contract_aux(I, I3), out, rtol=0, atol=1e-13)
+    I4 = r.normal(size=(4, nr, ns))
+    out = np.array([[np.sum(I[a] * I4[b]) for b in range(4)] for a in range(g)])
+    assert np.allclose(dfops.contract_pairs(I, I4), out, rtol=0, atol=1e-13)
+    assert np.allclose(dfops.density_fit(I, Mrs), [np.sum(I[a] * Mrs) for a in range(g)], rtol=0, atol=1e-13)
+    assert np.allclose(dfops.density_back(I, D), sum(D[a] * I[a] for a in range(g)), rtol=0, atol=1e-13)
+    out = np.zeros((g, nt, nu))
+    for a in range(g):
+        for t in range(nt):
+            for u in range(nu):
+                out[a, t, u] = sum(I[a, k, s] * G[k * ns + s, t * nu + u] for k in range(nr) for s in range(ns))
+    assert np.allclose(dfops.apply_four_index(I, G, nt, nu), out, rtol=0, atol=1e-13)
+
+
+def test_dfops_give_exact_coulomb_and_exchange_for_h2():
+    """With the product-complete auxiliary set of H2, J = density_back(B, density_fit(B, D)) and
+    K = contract_first(Y, Y) with Y = transform_first(B, C_occ) equal the four-index J and K."""
+    from oracle import dfops
+    sysh = clusters.h2_system(1.4, alpha=0.8)
+    B = dfrhf.whiten(dfrhf.three_center(sysh), dfrhf.metric(sysh))
+    eri = dfrhf.four_center(sysh)
+    C = np.linalg.qr(np.random.default_rng(4).normal(size=(2, 1)))[0]
+    D = 2 * C @ C.T
+    J = dfops.density_back(B, dfops.density_fit(B, D))
+    Y = dfops.transform_first(B, C)
+    K = dfops.contract_first(Y, Y)
+    assert np.abs(J - dfrhf.conv_J(eri, D)).max() < 1e-10
+    assert np.abs(K - dfrhf.conv_K(eri, C)).max() < 1e-10
+
+
+def test_dfops_identities():
+    """Adjointness of the two density contractions; orthogonal transformations undone by their
+    transposes; G-application of a two-object product equals the auxiliary transformation by the pair
+    contraction: sum_rs I_g,rs (sum_h I2_h,rs I3_h,tu) = sum_h (sum_rs I_g,rs I2_h,rs) I3_h,tu."""
+    from oracle import dfops
+    r = np.random.default_rng(32)
+    g, nr, ns, nt, nu = 7, 5, 6, 3, 4
+    I, I2, I3 = r.normal(size=(g, nr, ns)), r.normal(size=(g + 2, nr, ns)), r.normal(size=(g + 2, nt, nu))
+    M, D = r.normal(size=(nr, ns)), r.normal(size=g)
+    assert abs(dfops.density_fit(I, M) @ D - np.sum(M * dfops.density_back(I, D))) < 1e-12
+    Q = np.linalg.qr(r.normal(size=(nr, nr)))[0]
+    assert np.abs(dfops.transform_first(dfops.transform_first(I, Q), Q.T) - I).max() < 1e-13
+    Q2 = np.linalg.qr(r.normal(size=(ns, ns)))[0]
+    assert np.abs(dfops.transform_second(dfops.transform_second(I, Q2), Q2.T) - I).max() < 1e-13
+    lhs = dfops.apply_four_index(I, dfops.contract_aux(I2, I3), nt, nu)
+    rhs = dfops.transform_aux(I3, dfops.contract_pairs(I, I2))
+    assert np.abs(lhs - rhs).max() < 1e-12
