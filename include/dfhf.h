@@ -238,6 +238,37 @@ int scf_run_rohf(df_handle* h, const df_options* opts, int nalpha, int nbeta, do
  * about 8 naux (np + 2 nmo) nocc bytes besides B. */
 int df_mp2(df_handle* h, const double* C, const double* eps, int nmo, int nocc, double* e2);
 
+/* ---- density-fitting object operations (paper, section "Density fitting utilities", eqs. 1-3) ----------
+ * A df_tensor is a dense FP64 three-index object I[g][r][s] (g the auxiliary index, row-major) on the device
+ * of the handle it was made with; every operation runs on that handle's stream (one thread at a time per
+ * handle, as for the other calls) and returns when its result is complete. Host arrays are row-major and
+ * owned by the caller. Free every tensor (df_tensor_free) before its handle. Dimensions that do not match
+ * give DF_E_ARG; DF_E_NOMEM if a result does not fit. */
+typedef struct df_tensor df_tensor;
+/* A new object of naux x nr x ns, from host_init (naux nr ns doubles) or zeros if host_init is NULL. */
+int df_tensor_create(df_handle* h, int naux, int nr, int ns, const double* host_init, df_tensor** out);
+/* The handle's B as an object: naux x n x n, both triangles (DF_E_STATE before df_build_B). */
+int df_tensor_from_B(df_handle* h, df_tensor** out);
+int df_tensor_shape(const df_tensor* t, int* naux, int* nr, int* ns);
+/* Copy the object to host (naux nr ns doubles). */
+int df_tensor_get(const df_tensor* t, double* host);
+void df_tensor_free(df_tensor* t);
+/* Eq. 1, index transformations, into a new object:
+ *   which 0: I'_{g,ts} = sum_r I_{g,rs} M_rt   (M: nr x nt; m_rows = nr, m_cols = nt)
+ *   which 1: I'_{g,rt} = sum_s I_{g,rs} M_st   (M: ns x nt; m_rows = ns, m_cols = nt)
+ *   which 2: I'_{g,rs} = sum_d M'_gd I_{d,rs}  (M': naux' x naux; m_rows = naux', m_cols = naux) */
+int df_op_transform(const df_tensor* I, int which, const double* M, int m_rows, int m_cols, df_tensor** out);
+/* Eq. 2, contractions of two objects into a host matrix `out`:
+ *   which 0: M_st = sum_{g r} I_{g,rs} I2_{g,rt}       (I2: naux x nr x nt; out ns x nt)
+ *   which 1: G_{rs,tu} = sum_g I_{g,rs} I2_{g,tu}      (I2: naux x nt x nu; out (nr ns) x (nt nu))
+ *   which 2: M_gd = sum_{rs} I_{g,rs} I2_{d,rs}        (I2: naux2 x nr x ns; out naux x naux2) */
+int df_op_contract(const df_tensor* I, const df_tensor* I2, int which, double* out);
+/* Eq. 3: D_g = sum_rs I_{g,rs} M_rs (M: nr x ns; D: naux) and M_rs = sum_g D_g I_{g,rs}. */
+int df_op_density_fit(const df_tensor* I, const double* M, double* D);
+int df_op_density_back(const df_tensor* I, const double* D, double* M);
+/* Eq. 3: I'_{g,tu} = sum_rs I_{g,rs} G_{rs,tu} (G: (nr ns) x (nt nu)), into a new naux x nt x nu object. */
+int df_op_apply_four_index(const df_tensor* I, const double* G, int nt, int nu, df_tensor** out);
+
 /* SCF from a guess density D0 (host, n x n, symmetric; NULL = core-Hamiltonian guess): the first
  * occupied orbitals are the nocc natural orbitals of D0 with the largest occupations in the S metric
  * (eigenvectors of X^T S D0 S X). Otherwise as scf_run. */

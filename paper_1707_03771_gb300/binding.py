@@ -24,7 +24,9 @@ EXPORTED = ["df_init", "df_sizes", "df_build_B", "df_build_B_ex", "df_jk", "scf_
             "df_water_features", "df_water_blocks", "df_water_density", "df_mlp_guess", "df_rint_pow2",
             "df_fp64_rate", "df_sad_density", "df_build_B_batch",
             "df_init_open", "scf_run_uhf", "scf_run_rohf", "df_water_pairs", "df_pair_blocks", "df_pair_density",
-            "df_mlp_guess_pairs", "df_mp2"]
+            "df_mlp_guess_pairs", "df_mp2", "df_tensor_create", "df_tensor_from_B", "df_tensor_shape",
+            "df_tensor_get", "df_tensor_free", "df_op_transform", "df_op_contract", "df_op_density_fit",
+            "df_op_density_back", "df_op_apply_four_index"]
 DF_MLP_NFEAT = 57
 DF_MLP_NPFEAT = 26
 PAIR_CUTOFF = 7.5      # bohr, O-O distance of the water pairs whose blocks the pair network predicts
@@ -118,6 +120,17 @@ def load(path: str | None = None):
     L.df_pair_density.argtypes = [c_void_p, fp, ip, c_int, dp]
     L.df_mlp_guess_pairs.argtypes = [c_void_p, c_void_p, c_void_p, ctypes.c_double, c_int, dp]
     L.df_mp2.argtypes = [c_void_p, dp, dp, c_int, c_int, dp]
+    L.df_tensor_create.argtypes = [c_void_p, c_int, c_int, c_int, dp, P(c_void_p)]
+    L.df_tensor_from_B.argtypes = [c_void_p, P(c_void_p)]
+    L.df_tensor_shape.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
+    L.df_tensor_get.argtypes = [c_void_p, dp]
+    L.df_tensor_free.argtypes = [c_void_p]
+    L.df_tensor_free.restype = None
+    L.df_op_transform.argtypes = [c_void_p, c_int, dp, c_int, c_int, P(c_void_p)]
+    L.df_op_contract.argtypes = [c_void_p, c_void_p, c_int, dp]
+    L.df_op_density_fit.argtypes = [c_void_p, dp, dp]
+    L.df_op_density_back.argtypes = [c_void_p, dp, dp]
+    L.df_op_apply_four_index.argtypes = [c_void_p, dp, c_int, c_int, P(c_void_p)]
     L.df_set_stream.argtypes = [c_void_p, c_void_p]
     L.df_timings.argtypes = [c_void_p, dp, c_int]
     L.df_free.argtypes = [c_void_p]
@@ -355,6 +368,11 @@ class Handle:
 
     def close(self):
         if getattr(self, "h", None):
+            # density-fitting objects made on this handle go first (they use its stream)
+            for ref in getattr(self, "_tensors", []):
+                t = ref()
+                if t is not None:
+                    t.close()
             load().df_free(self.h)
             self.h = None
 
@@ -437,6 +455,93 @@ def water_pairs(system, cutoff=PAIR_CUTOFF):
         if rc < 0:
             raise DFError(rc, "df_water_pairs")
     return pairs, feats
+
+
+class DFTensor:
+    """A density-fitting object I[g][r][s] on the device (df_tensor_*), with the operations of eqs. (1)-(3)
+    (df_op_*). Results of eq. (2) and (3) that are matrices or vectors come back as numpy arrays; objects
+    as new DFTensor instances. Close (or let go) every tensor before its Handle."""
+
+    def __init__(self, handle, ptr):
+        import weakref
+        self.handle, self.t = handle, ptr
+        if not hasattr(handle, "_tensors"):
+            handle._tensors = []
+        handle._tensors.append(weakref.ref(self))
+        a, r, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        handle._check(load().df_tensor_shape(self.t, ctypes.byref(a), ctypes.byref(r), ctypes.byref(s)),
+                      "df_tensor_shape")
+        self.shape = (a.value, r.value, s.value)
+
+    @classmethod
+    def create(cls, handle, array):
+        array = np.ascontiguousarray(array, dtype=np.float64)
+        if array.ndim != 3:
+            raise ValueError("a density-fitting object is a 3-index array (g, r, s)")
+        p = ctypes.c_void_p()
+        handle._check(load().df_tensor_create(handle.h, *array.shape, _dp(array), ctypes.byref(p)),
+                      "df_tensor_create")
+        return cls(handle, p)
+
+    @classmethod
+    def from_B(cls, handle):
+        p = ctypes.c_void_p()
+        handle._check(load().df_tensor_from_B(handle.h, ctypes.byref(p)), "df_tensor_from_B")
+        return cls(handle, p)
+
+    def get(self):
+        out = np.empty(self.shape)
+        self.handle._check(load().df_tensor_get(self.t, _dp(out)), "df_tensor_get")
+        return out
+
+    def transform(self, which, M):
+        """Eq. (1): which "first" (M: nr x nt), "second" (M: ns x nt) or "aux" (M': naux' x naux)."""
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        p = ctypes.c_void_p()
+        w = {"first": 0, "second": 1, "aux": 2}[which]
+        self.handle._check(load().df_op_transform(self.t, w, _dp(M), M.shape[0], M.shape[1], ctypes.byref(p)),
+                           "df_op_transform")
+        return DFTensor(self.handle, p)
+
+    def contract(self, other, which):
+        """Eq. (2): which "first" (ns x nt), "aux" ((nr ns) x (nt nu)) or "pairs" (naux x naux2)."""
+        a, r, s = self.shape
+        a2, r2, s2 = other.shape
+        shape = {"first": (s, s2), "aux": (r * s, r2 * s2), "pairs": (a, a2)}[which]
+        out = np.empty(shape)
+        w = {"first": 0, "aux": 1, "pairs": 2}[which]
+        self.handle._check(load().df_op_contract(self.t, other.t, w, _dp(out)), "df_op_contract")
+        return out
+
+    def density_fit(self, M):
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        D = np.empty(self.shape[0])
+        self.handle._check(load().df_op_density_fit(self.t, _dp(M), _dp(D)), "df_op_density_fit")
+        return D
+
+    def density_back(self, D):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        M = np.empty(self.shape[1:])
+        self.handle._check(load().df_op_density_back(self.t, _dp(D), _dp(M)), "df_op_density_back")
+        return M
+
+    def apply_four_index(self, G, nt, nu):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        p = ctypes.c_void_p()
+        self.handle._check(load().df_op_apply_four_index(self.t, _dp(G), int(nt), int(nu), ctypes.byref(p)),
+                           "df_op_apply_four_index")
+        return DFTensor(self.handle, p)
+
+    def close(self):
+        if getattr(self, "t", None):
+            load().df_tensor_free(self.t)
+            self.t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mlp:
