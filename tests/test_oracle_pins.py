@@ -835,3 +835,44 @@ def test_dfops_identities():
     lhs = dfops.apply_four_index(I, dfops.contract_aux(I2, I3), nt, nu)
     rhs = dfops.transform_aux(I3, dfops.contract_pairs(I, I2))
     assert np.abs(lhs - rhs).max() < 1e-12
+
+
+# nuclear gradient of DF-RHF (oracle/dfgrad.py)
+
+@pytest.fixture(scope="module")
+def water1_grad():
+    from oracle import dfgrad
+    s = clusters.water_cluster(1, 3)
+    B = dfrhf.whiten(dfrhf.three_center(s), dfrhf.metric(s))
+    res = dfrhf.scf(s, B=B, conv_E=1e-13, conv_err=1e-10, max_iter=200)
+    return s, res, dfgrad.gradient(s, res)
+
+
+def test_gradient_matches_energy_differences(water1_grad):
+    """Against fourth-order central differences of the converged SCF energy along every coordinate of a
+    water (each displaced geometry converged from scratch): a dropped orbital-constraint term -tr(W S^x), a
+    sign slip on the metric-derivative terms or a missing nuclear-repulsion term all fail it."""
+    from oracle import dfgrad
+    s, res, g = water1_grad
+    h = 2e-3
+
+    def energy(a, d, step):
+        sd = dfgrad.displaced(s, a, d, step)
+        return dfrhf.scf(sd, conv_E=1e-13, conv_err=1e-10, max_iter=200).energy
+
+    fd = np.zeros_like(g)
+    for a in range(len(s.atoms)):
+        for d in range(3):
+            e = [energy(a, d, k * h) for k in (-2, -1, 1, 2)]
+            fd[a, d] = (8 * (e[2] - e[1]) - (e[3] - e[0])) / (12 * h)
+    assert np.abs(g).max() > 1e-3
+    assert np.abs(g - fd).max() < 5e-8, np.abs(g - fd).max()
+
+
+def test_gradient_translation_and_rotation_invariance(water1_grad):
+    """The energy does not change under rigid translations and rotations: the gradient sums to zero and
+    exerts no torque."""
+    s, res, g = water1_grad
+    R = np.asarray(s.atoms["xyz"], dtype=np.float64)
+    assert np.abs(g.sum(axis=0)).max() < 1e-8
+    assert np.abs(np.cross(R, g).sum(axis=0)).max() < 1e-8
